@@ -1,0 +1,202 @@
+/*
+ * grid.c -- finite-volume IMEX-RK3 update of one 1D/2D/3D Cartesian grid.
+ * TEST INFRASTRUCTURE ONLY (the oracle; see oracle.h).
+ *
+ * Paper: Eq. full (conservative update), Eq. explicit (hyperbolic part,
+ * read with its missing dt: U* = U - dt/dx (F_{i+1/2} - F_{i-1/2})), the RK3
+ * IMEX stages of Sec. 3.1 with implicit weights 1, 1/4, 2/3, and
+ * Sec. 3.3 for the implicit part.  Multi-dimensional grids sum the
+ * directional flux differences in every stage (unsplit method of lines).
+ * Boundaries: outflow (copy of the edge cell) or periodic, through index
+ * mapping of the two ghost layers that PLM needs.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include "oracle.h"
+
+static int map_idx(int c, int n, int bc)
+{
+    if (bc == OR_BC_PERIODIC) {
+        int m = c % n;
+        return m < 0 ? m + n : m;
+    }
+    return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+static int64_t ncells(const or_grid* g) { return (int64_t)g->n[0] * g->n[1] * g->n[2]; }
+
+static int64_t lin(const or_grid* g, int i, int j, int k)
+{
+    return ((int64_t)k * g->n[1] + j) * g->n[0] + i;
+}
+
+static void load(const double* A, int64_t N, int64_t c, double* x)
+{
+    for (int q = 0; q < 12; q++) x[q] = A[q * N + c];
+}
+
+/* dt = CFL / max_cells sum_d lambda_d / dx_d (signal speeds of or_signal_speed) */
+double or_grid_dt(const or_params* P, const or_grid* g, const double* V)
+{
+    int64_t N = ncells(g);
+    double smax = 0.0;
+    for (int64_t c = 0; c < N; c++) {
+        double v[12];
+        load(V, N, c, v);
+        double s = or_signal_speed(P, 0, v) / g->dx[0];
+        for (int d = 1; d < g->ndim; d++) s = s + or_signal_speed(P, d, v) / g->dx[d];
+        if (s > smax) smax = s;
+    }
+    return P->cfl / smax;
+}
+
+static void face_dims(const or_grid* g, int dir, int m[3])
+{
+    m[0] = g->n[0];
+    m[1] = g->n[1];
+    m[2] = g->n[2];
+    m[dir] += 1;
+}
+
+/* Numerical flux at every face normal to dir.  Face (i,j,k) of direction d
+ * lies between cells with index i_d - 1 and i_d along d; faces are stored
+ * [12][m2][m1][m0] with m = n + e_d. */
+int or_grid_face_flux(const or_params* P, const or_grid* g, int dir, const double* U,
+                      const double* V, const double* kappa, const double* sigma,
+                      double* Fhat, or_stats* st)
+{
+    int64_t N = ncells(g);
+    int m[3];
+    face_dims(g, dir, m);
+    int64_t NF = (int64_t)m[0] * m[1] * m[2];
+    int nd = g->n[dir], bc = g->bc[dir];
+    int nfb = 0;
+    for (int k = 0; k < m[2]; k++)
+        for (int j = 0; j < m[1]; j++)
+            for (int i = 0; i < m[0]; i++) {
+                int pos[3] = {i, j, k};
+                int f = pos[dir];
+                int64_t cidx[4];
+                for (int s = 0; s < 4; s++) {
+                    int q[3] = {i, j, k};
+                    q[dir] = map_idx(f - 2 + s, nd, bc);
+                    cidx[s] = lin(g, q[0], q[1], q[2]);
+                }
+                double w[4][12], Vm[12], Vp[12], VL[12], VR[12], F[12];
+                for (int s = 0; s < 4; s++) load(V, N, cidx[s], w[s]);
+                or_reconstruct(P, w[0], w[1], w[2], Vm, VL, 0); /* cell f-1: right face */
+                or_reconstruct(P, w[1], w[2], w[3], VR, Vp, 0); /* cell f:   left face  */
+                double tauL = (U[cidx[1]] * (kappa[cidx[1]] + sigma[cidx[1]])) * g->dx[dir];
+                double tauR = (U[cidx[2]] * (kappa[cidx[2]] + sigma[cidx[2]])) * g->dx[dir];
+                nfb += or_pvm_flux(P, dir, VL, VR, tauL, tauR, F, 0, st);
+                int64_t fi = ((int64_t)k * m[1] + j) * m[0] + i;
+                for (int q = 0; q < 12; q++) Fhat[q * NF + fi] = F[q];
+            }
+    return nfb;
+}
+
+/* One IMEX-RK3 stage (Sec. 3.1):
+ *   stage 1: U* = U^(0) + dt L(U^(0)),                         U^(1) = U* + dt S
+ *   stage 2: U* = 3/4 U^(0) + 1/4 (U^(1) + dt L(U^(1))),       U^(2) = U* + dt/4 S
+ *   stage 3: U* = 1/3 U^(0) + 2/3 (U^(2) + dt L(U^(2))),       U^(3) = U* + 2dt/3 S
+ * with dt L = -sum_d dt/dx_d (F_{+} - F_{-}) and the source solved implicitly
+ * at the new stage state. */
+int or_grid_stage(const or_params* P, const or_grid* g, int stage, double dt,
+                  const double* U0, const double* Us, const double* Vs,
+                  const double* kappa, const double* sigma,
+                  double* Uout, double* Vout, int32_t* cell_status, or_stats* st)
+{
+    int64_t N = ncells(g);
+    double* Fh[3] = {0, 0, 0};
+    int m[3][3];
+    for (int d = 0; d < g->ndim; d++) {
+        face_dims(g, d, m[d]);
+        Fh[d] = (double*)malloc(sizeof(double) * 12 * (size_t)m[d][0] * m[d][1] * m[d][2]);
+        or_grid_face_flux(P, g, d, Us, Vs, kappa, sigma, Fh[d], st);
+    }
+    double a = 0.0, b = 1.0, w = 1.0;
+    if (stage == 2) { a = 0.75; b = 0.25; w = 0.25; }
+    if (stage == 3) { a = 1.0 / 3.0; b = 2.0 / 3.0; w = 2.0 / 3.0; }
+    double hdt = w * dt;
+    double dtdx[3];
+    for (int d = 0; d < 3; d++) dtdx[d] = dt / g->dx[d];
+
+    int nfail = 0;
+    for (int k = 0; k < g->n[2]; k++)
+        for (int j = 0; j < g->n[1]; j++)
+            for (int i = 0; i < g->n[0]; i++) {
+                int64_t c = lin(g, i, j, k);
+                int64_t fl[3], fr[3], NF[3];
+                for (int d = 0; d < g->ndim; d++) {
+                    int p[3] = {i, j, k};
+                    NF[d] = (int64_t)m[d][0] * m[d][1] * m[d][2];
+                    fl[d] = ((int64_t)p[2] * m[d][1] + p[1]) * m[d][0] + p[0];
+                    p[d] += 1;
+                    fr[d] = ((int64_t)p[2] * m[d][1] + p[1]) * m[d][0] + p[0];
+                }
+                double Ust[12], Un[12], Vn[12], vs[12];
+                for (int q = 0; q < 12; q++) {
+                    double acc = (Fh[0][q * NF[0] + fr[0]] - Fh[0][q * NF[0] + fl[0]]) * dtdx[0];
+                    for (int d = 1; d < g->ndim; d++)
+                        acc = acc + (Fh[d][q * NF[d] + fr[d]] - Fh[d][q * NF[d] + fl[d]]) * dtdx[d];
+                    if (stage == 1)
+                        Ust[q] = Us[q * N + c] - acc;
+                    else
+                        Ust[q] = a * U0[q * N + c] + b * (Us[q * N + c] - acc);
+                }
+                load(Vs, N, c, vs);
+                double Zg = or_prim_Z(P, vs);
+                int rc = or_implicit(P, kappa[c], sigma[c], hdt, Ust, Zg, Un, Vn, st);
+                if (cell_status) cell_status[c] = rc;
+                if (rc != OR_OK) nfail++;
+                for (int q = 0; q < 12; q++) {
+                    Uout[q * N + c] = Un[q];
+                    Vout[q * N + c] = Vn[q];
+                }
+            }
+    for (int d = 0; d < g->ndim; d++) free(Fh[d]);
+    return nfail;
+}
+
+/* One full IMEX-RK3 step of size dt; U and V are updated in place. */
+int or_grid_step(const or_params* P, const or_grid* g, double dt, double* U, double* V,
+                 const double* kappa, const double* sigma, or_stats* st)
+{
+    int64_t N = ncells(g);
+    size_t bytes = sizeof(double) * 12 * (size_t)N;
+    double* U1 = (double*)malloc(bytes);
+    double* V1 = (double*)malloc(bytes);
+    double* U2 = (double*)malloc(bytes);
+    double* V2 = (double*)malloc(bytes);
+    int nfail = 0;
+    nfail += or_grid_stage(P, g, 1, dt, U, U, V, kappa, sigma, U1, V1, 0, st);
+    if (!nfail) nfail += or_grid_stage(P, g, 2, dt, U, U1, V1, kappa, sigma, U2, V2, 0, st);
+    if (!nfail) nfail += or_grid_stage(P, g, 3, dt, U, U2, V2, kappa, sigma, U, V, 0, st);
+    free(U1);
+    free(V1);
+    free(U2);
+    free(V2);
+    return nfail;
+}
+
+/* Advance from t0 to t_end (the last step is clipped to land on t_end), at
+ * most max_steps steps.  Returns the number of failed cells (0 on success). */
+int or_grid_run(const or_params* P, const or_grid* g, double t0, double t_end, int max_steps,
+                double* U, double* V, const double* kappa, const double* sigma,
+                double* t_out, int* steps_out, or_stats* st)
+{
+    double t = t0;
+    int s = 0, nfail = 0;
+    while (t < t_end && s < max_steps) {
+        double dt = or_grid_dt(P, g, V);
+        if (t + dt > t_end) dt = t_end - t;
+        nfail = or_grid_step(P, g, dt, U, V, kappa, sigma, st);
+        if (nfail) break;
+        t = t + dt;
+        s++;
+    }
+    if (t_out) *t_out = t;
+    if (steps_out) *steps_out = s;
+    return nfail;
+}

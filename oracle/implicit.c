@@ -1,0 +1,348 @@
+/*
+ * implicit.c -- per-cell implicit radiation-matter step of the IMEX scheme
+ * (Sec. 3.3, Eqs. timeadv, totale, totalm).  TEST INFRASTRUCTURE ONLY
+ * (the oracle; see oracle.h).
+ *
+ * The cell solves, for X = (E_r, F_r^i),
+ *     R(X) = X - X* + h G(X, V(X)) = 0,            h = (stage weight) dt,
+ * since S_r = (-G^0, -G^i) (Eq. sourceterms).  The magnetofluid follows from
+ * the conserved totals (Eqs. totale, totalm):
+ *     tau_e = tau_{e,t} - E_r,  S = S_t - F_r,  D and B unchanged,
+ * and V(X) is the con2prim of that state (Sec. 3.3 step 5).
+ *
+ * Default (OR_IMP_NEWTON): Newton's method on R with a forward-difference
+ * Jacobian.  The paper's iteration (OR_IMP_PICARD) freezes the matter and the
+ * Eddington tensor in the matrix C^(m) of Sec. 3.3 step 2; it is kept as an
+ * option.  The Picard form diverges once the radiation heat capacity term
+ * 4 a_R T^3 h kappa (gamma-1)/rho exceeds about one, which the stiff
+ * workloads reach, hence Newton by default.
+ */
+#include <math.h>
+#include "oracle.h"
+
+#define IMP_LADDER 6   /* continuation fallback starts at h / 2^6 */
+
+typedef struct {
+    const or_params* P;
+    double kappa, sigma, hdt;
+    double D, St[3], taut, B[3];
+    double Xs[4];
+    or_stats* st;
+} imp_ctx;
+
+static void matter_state(const imp_ctx* c, const double X[4], double Um[12])
+{
+    Um[0] = c->D;
+    Um[1] = c->St[0] - X[1];
+    Um[2] = c->St[1] - X[2];
+    Um[3] = c->St[2] - X[3];
+    Um[4] = c->taut - X[0];
+    Um[5] = c->B[0];
+    Um[6] = c->B[1];
+    Um[7] = c->B[2];
+    Um[8] = X[0];
+    Um[9] = X[1];
+    Um[10] = X[2];
+    Um[11] = X[3];
+}
+
+/* R(X); also returns the primitives of the matter state at X. */
+static int imp_residual(imp_ctx* c, const double X[4], double Zg, double R[4],
+                        double V[12], double* Z)
+{
+    double Um[12];
+    if (c->st) c->st->imp_resid++;
+    if (!(X[0] > 0.0)) return 1;
+    matter_state(c, X, Um);
+    if (or_con2prim(c->P, Um, Zg, V, Z, c->st) != OR_OK) return 1;
+    double v2 = (V[1] * V[1] + V[2] * V[2]) + V[3] * V[3];
+    double W = 1.0 / sqrt(1.0 - v2);
+    double u[3] = {W * V[1], W * V[2], W * V[3]};
+    double T = V[4] / V[0];                       /* T = p/rho in code units */
+    double BP = c->P->a_rad * ((T * T) * (T * T)); /* 4 pi B = a_R T^4 */
+    double Pr[3][3], G[4];
+    or_m1_pressure(X[0], X + 1, Pr);
+    or_four_force(c->kappa, c->sigma, V[0], u, W, BP, X[0], X + 1, Pr, G);
+    for (int i = 0; i < 4; i++) R[i] = (X[i] - c->Xs[i]) + c->hdt * G[i];
+    return 0;
+}
+
+/* Gaussian elimination with partial pivoting; A and b are overwritten. */
+int or_solve4(double A[4][4], double b[4], double x[4])
+{
+    for (int col = 0; col < 4; col++) {
+        int piv = col;
+        for (int r = col + 1; r < 4; r++)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (A[piv][col] == 0.0) return 1;
+        if (piv != col) {
+            for (int k = 0; k < 4; k++) {
+                double t = A[col][k];
+                A[col][k] = A[piv][k];
+                A[piv][k] = t;
+            }
+            double t = b[col];
+            b[col] = b[piv];
+            b[piv] = t;
+        }
+        for (int r = col + 1; r < 4; r++) {
+            double f = A[r][col] / A[col][col];
+            for (int k = col + 1; k < 4; k++) A[r][k] = A[r][k] - f * A[col][k];
+            b[r] = b[r] - f * b[col];
+        }
+    }
+    for (int r = 3; r >= 0; r--) {
+        double s = b[r];
+        for (int k = r + 1; k < 4; k++) s = s - A[r][k] * x[k];
+        x[r] = s / A[r][r];
+    }
+    return 0;
+}
+
+/* Matrix C^(m) and right-hand side of Sec. 3.3 steps 2-3, i.e. the linear
+ * system R(X) = C X - rhs = 0 obtained with the matter (rho, W, u, 4piB) and
+ * the Eddington tensor D_r frozen.  The block C_{i+1,j+1} is derived from
+ * Eqs. g0 and gi: delta_j^i + h rho W [(kappa+sigma) delta_j^i + 2 sigma u^i u_j]
+ * (the printed minus sign in front of h would make absorption amplify F_r).
+ * W^2 - 1 = u^2 and 2W^2 - 1 = 2u^2 + 1. */
+void or_picard_matrix(double kappa, double sigma, double hdt, double rho, const double u[3],
+                      double W, double BP, const double Dr[3][3],
+                      const double Xs[4], double C[4][4], double rhs[4])
+{
+    double u2 = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
+    double Du[3];
+    for (int i = 0; i < 3; i++) Du[i] = (Dr[i][0] * u[0] + Dr[i][1] * u[1]) + Dr[i][2] * u[2];
+    double uDu = (u[0] * Du[0] + u[1] * Du[1]) + u[2] * Du[2];
+    double ks = kappa + sigma;
+    C[0][0] = 1.0 - hdt * ((rho * W) * (-kappa + sigma * (u2 + uDu)));
+    for (int j = 0; j < 3; j++)
+        C[0][1 + j] = -hdt * ((rho * u[j]) * (kappa - sigma * (2.0 * u2 + 1.0)));
+    for (int i = 0; i < 3; i++) {
+        C[1 + i][0] = -hdt * (rho * (ks * Du[i] + (sigma * u[i]) * ((W * W) + uDu)));
+        for (int j = 0; j < 3; j++) {
+            double t = hdt * ((rho * W) * ((i == j ? ks : 0.0) + (2.0 * sigma) * (u[i] * u[j])));
+            C[1 + i][1 + j] = (i == j ? 1.0 : 0.0) + t;
+        }
+    }
+    rhs[0] = Xs[0] + hdt * (((rho * W) * kappa) * BP);
+    for (int i = 0; i < 3; i++) rhs[1 + i] = Xs[1 + i] + hdt * (((rho * u[i]) * kappa) * BP);
+}
+
+static void eddington_tensor(double E, const double F[3], double Dr[3][3])
+{
+    double F2 = (F[0] * F[0] + F[1] * F[1]) + F[2] * F[2];
+    double f2 = F2 / (E * E);
+    if (f2 > 1.0) f2 = 1.0;
+    double xi = (3.0 + 4.0 * f2) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f2));
+    double a = 0.5 * (1.0 - xi);
+    double c = (F2 > 0.0) ? (0.5 * (3.0 * xi - 1.0)) / F2 : 0.0;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) Dr[i][j] = c * (F[i] * F[j]) + (i == j ? a : 0.0);
+}
+
+static int picard(imp_ctx* c, double X[4], double V[12], double* Z)
+{
+    const or_params* P = c->P;
+    for (int m = 1; m <= P->imp_maxit; m++) {
+        double v2 = (V[1] * V[1] + V[2] * V[2]) + V[3] * V[3];
+        double W = 1.0 / sqrt(1.0 - v2);
+        double u[3] = {W * V[1], W * V[2], W * V[3]};
+        double T = V[4] / V[0];
+        double BP = P->a_rad * ((T * T) * (T * T));
+        double Dr[3][3], C[4][4], rhs[4], Xn[4], Um[12];
+        eddington_tensor(X[0], X + 1, Dr);
+        or_picard_matrix(c->kappa, c->sigma, c->hdt, V[0], u, W, BP, Dr, c->Xs, C, rhs);
+        if (or_solve4(C, rhs, Xn)) return 1;
+        if (c->st) c->st->imp_iters++;
+        double dmax = 0.0;
+        for (int i = 0; i < 4; i++) {
+            double d = fabs(Xn[i] - X[i]);
+            if (d > dmax) dmax = d;
+            X[i] = Xn[i];
+        }
+        if (!(X[0] > 0.0)) return 1;
+        matter_state(c, X, Um);
+        if (or_con2prim(P, Um, *Z, V, Z, c->st) != OR_OK) return 1;
+        if (dmax <= P->imp_tol * X[0]) return 0;
+    }
+    return 1;
+}
+
+/* C^(m) at the current iterate, from its matter primitives V and Eddington tensor */
+static void picard_jacobian(const imp_ctx* c, const double X[4], const double V[12], double J[4][4])
+{
+    double v2 = (V[1] * V[1] + V[2] * V[2]) + V[3] * V[3];
+    double W = 1.0 / sqrt(1.0 - v2);
+    double u[3] = {W * V[1], W * V[2], W * V[3]};
+    double Dr[3][3], rhs[4];
+    eddington_tensor(X[0], X + 1, Dr);
+    or_picard_matrix(c->kappa, c->sigma, c->hdt, V[0], u, W, 0.0, Dr, c->Xs, J, rhs);
+}
+
+/* Newton iteration on R(X) = 0.  The first matrix is the paper's C^(m) (the
+ * exact Jacobian with matter and Eddington tensor frozen), so the first
+ * iterates are the iteration of Sec. 3.3; when they contract slowly (ratio of
+ * successive steps > 1/4) or give no descent, the full Jacobian is formed by
+ * forward differences (step 1e-7 E_r) and kept while it contracts well.
+ * Every step is damped by a backtracking line search on |R|^2. */
+static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z)
+{
+    const or_params* P = c->P;
+    double J[4][4];
+    int full = 0, jac_age = 0, need_full = 0;
+    double prev = -1.0;
+    for (int m = 1; m <= P->imp_maxit; m++) {
+        if (need_full) {
+            double h = 1e-7 * X[0];
+            for (int j = 0; j < 4; j++) {
+                double Xp[4] = {X[0], X[1], X[2], X[3]};
+                double Rp[4], Vp[12], Zp;
+                Xp[j] = X[j] + h;
+                if (imp_residual(c, Xp, *Z, Rp, Vp, &Zp)) {
+                    Xp[j] = X[j] - h;
+                    if (imp_residual(c, Xp, *Z, Rp, Vp, &Zp)) return 1;
+                }
+                double dXj = Xp[j] - X[j];
+                for (int i = 0; i < 4; i++) J[i][j] = (Rp[i] - R[i]) / dXj;
+            }
+            full = 1;
+            need_full = 0;
+            jac_age = 0;
+            if (c->st) c->st->imp_jac++;
+        } else if (!full) {
+            picard_jacobian(c, X, V, J);
+        }
+        double A[4][4], b[4], dX[4];
+        for (int i = 0; i < 4; i++) {
+            b[i] = -R[i];
+            for (int j = 0; j < 4; j++) A[i][j] = J[i][j];
+        }
+        if (or_solve4(A, b, dX)) return 1;
+        if (c->st) c->st->imp_iters++;
+
+        /* converged when the full step is below tolerance: take it and stop */
+        double dfull = 0.0;
+        for (int i = 0; i < 4; i++) dfull = fabs(dX[i]) > dfull ? fabs(dX[i]) : dfull;
+        double Xn[4], Rn[4], Vn[12], Zn = *Z;
+        if (dfull <= P->imp_tol * X[0]) {
+            for (int i = 0; i < 4; i++) Xn[i] = X[i] + dX[i];
+            if (imp_residual(c, Xn, *Z, Rn, Vn, &Zn)) return 1;
+            for (int i = 0; i < 4; i++) {
+                X[i] = Xn[i];
+                R[i] = Rn[i];
+            }
+            for (int k = 0; k < 12; k++) V[k] = Vn[k];
+            *Z = Zn;
+            return 0;
+        }
+        /* damped update (backtracking line search): halve the step until the
+         * matter state is admissible and |R|^2 decreases (Armijo, 1e-4) */
+        double r0 = ((R[0] * R[0] + R[1] * R[1]) + R[2] * R[2]) + R[3] * R[3];
+        double lam = 1.0;
+        int ok = 0;
+        for (int k = 0; k < 40; k++) {
+            for (int i = 0; i < 4; i++) Xn[i] = X[i] + dX[i];
+            if (!imp_residual(c, Xn, *Z, Rn, Vn, &Zn)) {
+                double r1 = ((Rn[0] * Rn[0] + Rn[1] * Rn[1]) + Rn[2] * Rn[2]) + Rn[3] * Rn[3];
+                if (r1 <= (1.0 - 1e-4 * lam) * r0) { ok = 1; break; }
+            }
+            for (int i = 0; i < 4; i++) dX[i] = 0.5 * dX[i];
+            lam = 0.5 * lam;
+            if (!full && k == 3) break;   /* the frozen-matter matrix gives no descent */
+        }
+        if (!ok) {
+            /* no acceptable step: form the full Jacobian here and retry */
+            if (!full || jac_age > 0) { need_full = 1; continue; }
+            return 1;
+        }
+        jac_age++;
+        double dmax = 0.0;
+        for (int i = 0; i < 4; i++) {
+            double d = fabs(dX[i]);
+            if (d > dmax) dmax = d;
+        }
+        for (int i = 0; i < 4; i++) {
+            X[i] = Xn[i];
+            R[i] = Rn[i];
+        }
+        for (int k = 0; k < 12; k++) V[k] = Vn[k];
+        *Z = Zn;
+        /* slow contraction: switch to (or refresh) the full Jacobian at the new point */
+        if (prev >= 0.0 && dmax > 0.25 * prev) need_full = 1;
+        prev = dmax;
+    }
+    return 1;
+}
+
+int or_implicit(const or_params* P, double kappa, double sigma, double hdt,
+                const double Ustar[12], double Zguess, double U[12], double V[12], or_stats* st)
+{
+    if (st) st->imp_cells++;
+    if ((kappa == 0.0 && sigma == 0.0) || hdt == 0.0) {
+        for (int k = 0; k < 12; k++) U[k] = Ustar[k];
+        int rc = or_con2prim(P, Ustar, Zguess, V, 0, st);
+        if (rc != OR_OK && st) st->imp_fail++;
+        return rc;
+    }
+    imp_ctx c;
+    c.P = P;
+    c.kappa = kappa;
+    c.sigma = sigma;
+    c.hdt = hdt;
+    c.st = st;
+    c.D = Ustar[0];
+    c.taut = Ustar[4] + Ustar[8];
+    for (int j = 0; j < 3; j++) {
+        c.St[j] = Ustar[1 + j] + Ustar[9 + j];
+        c.B[j] = Ustar[5 + j];
+    }
+    for (int i = 0; i < 4; i++) c.Xs[i] = Ustar[8 + i];
+
+    double X[4] = {c.Xs[0], c.Xs[1], c.Xs[2], c.Xs[3]};
+    double R[4], Z = Zguess;
+    int fail = imp_residual(&c, X, Zguess, R, V, &Z);
+    if (fail) {
+        if (st) st->imp_fail++;
+        return OR_EIMPLICIT;
+    }
+    if (P->imp_mode == OR_IMP_PICARD) {
+        fail = picard(&c, X, V, &Z);
+    } else {
+        fail = newton(&c, X, R, V, &Z);
+        if (fail) {
+            /* continuation in the implicit weight: solve with h/64, h/32, ..., h,
+             * each from the previous solution (the solution moves continuously
+             * away from X* as h grows, and Newton stays in its basin) */
+            for (int i = 0; i < 4; i++) X[i] = c.Xs[i];
+            Z = Zguess;
+            fail = 0;
+            for (int j = IMP_LADDER; j >= 0 && !fail; j--) {
+                c.hdt = hdt / (double)(1 << j);
+                fail = imp_residual(&c, X, Z, R, V, &Z);
+                if (!fail) fail = newton(&c, X, R, V, &Z);
+            }
+            c.hdt = hdt;
+        }
+    }
+    if (fail) {
+        if (st) st->imp_fail++;
+        return OR_EIMPLICIT;
+    }
+    matter_state(&c, X, U);
+    return OR_OK;
+}
+
+void or_implicit_n(const or_params* P, int64_t n, const double* kappa, const double* sigma,
+                   double hdt, const double* Ustar, const double* Zg, double* U, double* V,
+                   int32_t* status, or_stats* st)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double us[12], u[12] = {0}, v[12] = {0};
+        for (int k = 0; k < 12; k++) us[k] = Ustar[k * n + i];
+        status[i] = or_implicit(P, kappa[i], sigma[i], hdt, us, Zg ? Zg[i] : 0.0, u, v, st);
+        for (int k = 0; k < 12; k++) {
+            U[k * n + i] = u[k];
+            V[k * n + i] = v[k];
+        }
+    }
+}

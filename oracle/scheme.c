@@ -1,0 +1,166 @@
+/*
+ * scheme.c -- explicit step of one interface: piecewise-linear reconstruction
+ * of the primitives with the Godunov fallback, and the PVM-int-8 Jacobian-free
+ * numerical flux.  TEST INFRASTRUCTURE ONLY (the oracle; see oracle.h).
+ *
+ * Paper: Sec. 3.2 (reconstruct-solve-update) and Sec. 3.2.2 (PVM solver,
+ * Eqs. generalflux, iterat, utilde, beta).
+ */
+#include <math.h>
+#include "oracle.h"
+
+/* Slope limiters of the PLM reconstruction (Sec. 3.2): MinMod (Roe 1986),
+ * MC (van Leer 1977) and VanLeer (van Leer 1974).  dL = V_i - V_{i-1},
+ * dR = V_{i+1} - V_i; zero slope at extrema. */
+double or_limiter(int recon, double dL, double dR)
+{
+    if (recon == OR_RECON_GODUNOV) return 0.0;
+    if (!(dL * dR > 0.0)) return 0.0;
+    if (recon == OR_RECON_MINMOD) return fabs(dL) < fabs(dR) ? dL : dR;
+    if (recon == OR_RECON_MC) {
+        double m = 2.0 * fabs(dL);
+        double r = 2.0 * fabs(dR);
+        double c = fabs(0.5 * (dL + dR));
+        if (r < m) m = r;
+        if (c < m) m = c;
+        return dL > 0.0 ? m : -m;
+    }
+    /* VanLeer: harmonic mean 2 dL dR/(dL + dR) */
+    return ((2.0 * dL) * dR) / (dL + dR);
+}
+
+/* Face values of cell i from its neighbours: Vminus at x_{i-1/2}, Vplus at
+ * x_{i+1/2}.  If either face value is superluminal (|v|^2 >= 1) or violates
+ * |F_r| <= E_r, the cell falls back to zeroth order (Sec. 3.2, Godunov
+ * reconstruction for non-physical reconstructed states). */
+void or_reconstruct(const or_params* P, const double Vm1[12], const double V0[12],
+                    const double Vp1[12], double Vminus[12], double Vplus[12], int* fallback)
+{
+    for (int k = 0; k < 12; k++) {
+        double s = or_limiter(P->recon, V0[k] - Vm1[k], Vp1[k] - V0[k]);
+        Vplus[k] = V0[k] + 0.5 * s;
+        Vminus[k] = V0[k] - 0.5 * s;
+    }
+    int bad = 0;
+    const double* faces[2] = {Vminus, Vplus};
+    for (int q = 0; q < 2; q++) {
+        const double* w = faces[q];
+        double v2 = (w[1] * w[1] + w[2] * w[2]) + w[3] * w[3];
+        double F2 = (w[9] * w[9] + w[10] * w[10]) + w[11] * w[11];
+        if (!(v2 < 1.0) || F2 > w[8] * w[8]) bad = 1;
+    }
+    if (bad)
+        for (int k = 0; k < 12; k++) {
+            Vplus[k] = V0[k];
+            Vminus[k] = V0[k];
+        }
+    if (fallback) *fallback = bad;
+}
+
+/* Coefficients of p_3(x) = x^2(x^2(x^2(a0 x^2 + a1) + a2) + a3) + a4, the
+ * internal approximation of |x| on [-1,1] built by Eq. iterat with k = 3. */
+static const double ALPHA[5] = {-1.0 / 128.0, 3.0 / 32.0, -23.0 / 64.0, 31.0 / 32.0, 39.0 / 128.0};
+
+typedef struct {
+    const or_params* P;
+    int dir;
+    double Um[12], Fm[12], Zm;
+    or_stats* st;
+} pvm_ctx;
+
+/* Jacobian-free product A(U_m)^2 w (Sec. 3.2.2 steps 3-5, Eq. utilde):
+ *   U_eps  = U_m + eps w                 -> V_eps = c2p(U_eps),  F(U_eps)
+ *   U~_eps = U_m + F(U_eps) - F(U_m)     -> V~_eps = c2p(U~_eps), F(U~_eps)
+ *   A^2 w  ~ (F(U~_eps) - F(U_m)) / eps                                      */
+static int a2_product(pvm_ctx* c, const double w[12], double out[12])
+{
+    const or_params* P = c->P;
+    double Ue[12], Ve[12], Fe[12], Ut[12], Vt[12], Ft[12];
+    for (int k = 0; k < 12; k++) Ue[k] = c->Um[k] + P->pvm_eps * w[k];
+    if (or_con2prim(P, Ue, c->Zm, Ve, 0, c->st) != OR_OK) return 1;
+    or_flux(P, c->dir, Ve, Ue, Fe);
+    for (int k = 0; k < 12; k++) Ut[k] = c->Um[k] + (Fe[k] - c->Fm[k]);
+    if (or_con2prim(P, Ut, c->Zm, Vt, 0, c->st) != OR_OK) return 1;
+    or_flux(P, c->dir, Vt, Ut, Ft);
+    if (c->st) c->st->flux_evals += 2;
+    for (int k = 0; k < 12; k++) out[k] = (Ft[k] - c->Fm[k]) / P->pvm_eps;
+    return 0;
+}
+
+/* PVM-int-8 numerical flux at one interface (Sec. 3.2.2, steps 1-7):
+ *   F^ = (F_L + F_R)/2 - beta U_{k+1}/2,  U_{k+1} ~ p_3(A(U_m)) (U_R - U_L),
+ * with lambda_max = 1, the Horner recursion in A^2
+ *   U_1 = a0 A^2 U_0 + a1 U_0,  U_{l+1} = A^2 U_l + a_{l+1} U_0  (l = 1..3),
+ * and beta = min{1/tau_L, 1/tau_R, 1} (Eq. beta), tau = rho W (kappa + sigma) dx
+ * at the two cell centres adjacent to the face.
+ * If a con2prim inside the viscosity term fails, the face uses Q = I
+ * (U_{k+1} = U_0, the lambda_max = 1 Rusanov flux) and returns 1. */
+int or_pvm_flux(const or_params* P, int dir, const double VL[12], const double VR[12],
+                double tauL, double tauR, double Fhat[12], double U4out[12], or_stats* st)
+{
+    double UL[12], UR[12], FL[12], FR[12], U0[12], Vm[12];
+    pvm_ctx c;
+    c.P = P;
+    c.dir = dir;
+    c.st = st;
+    or_prim2con(P, VL, UL);
+    or_prim2con(P, VR, UR);
+    or_flux(P, dir, VL, UL, FL);
+    or_flux(P, dir, VR, UR, FR);
+    if (st) { st->flux_evals += 2; st->pvm_faces++; }
+    for (int k = 0; k < 12; k++) {
+        U0[k] = UR[k] - UL[k];
+        c.Um[k] = 0.5 * (UL[k] + UR[k]);
+    }
+    double Zg = 0.5 * (or_prim_Z(P, VL) + or_prim_Z(P, VR));
+
+    double beta = 1.0;
+    if (P->beta_mode) {
+        double t = tauL > tauR ? tauL : tauR;
+        if (t < 1.0) t = 1.0;
+        beta = 1.0 / t;
+    }
+
+    double Ul[12], Y[12];
+    int fail = 0;
+    if (or_con2prim(P, c.Um, Zg, Vm, &c.Zm, st) != OR_OK) {
+        fail = 1;
+    } else {
+        or_flux(P, dir, Vm, c.Um, c.Fm);
+        if (st) st->flux_evals++;
+        for (int k = 0; k < 12; k++) Ul[k] = U0[k];
+        for (int l = 0; l < 4 && !fail; l++) {
+            if (a2_product(&c, Ul, Y)) { fail = 1; break; }
+            if (l == 0)
+                for (int k = 0; k < 12; k++) Ul[k] = ALPHA[0] * Y[k] + ALPHA[1] * U0[k];
+            else
+                for (int k = 0; k < 12; k++) Ul[k] = Y[k] + ALPHA[l + 1] * U0[k];
+        }
+    }
+    if (fail) {
+        for (int k = 0; k < 12; k++) Ul[k] = U0[k];
+        if (st) st->pvm_fallback++;
+    }
+    for (int k = 0; k < 12; k++) Fhat[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * (beta * Ul[k]);
+    if (U4out)
+        for (int k = 0; k < 12; k++) U4out[k] = Ul[k];
+    return fail;
+}
+
+void or_pvm_flux_n(const or_params* P, int dir, int64_t n, const double* VL, const double* VR,
+                   const double* tauL, const double* tauR, double* Fhat, double* U4,
+                   int32_t* status, or_stats* st)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double vl[12], vr[12], f[12], u4[12];
+        for (int k = 0; k < 12; k++) {
+            vl[k] = VL[k * n + i];
+            vr[k] = VR[k * n + i];
+        }
+        status[i] = or_pvm_flux(P, dir, vl, vr, tauL[i], tauR[i], f, u4, st);
+        for (int k = 0; k < 12; k++) {
+            Fhat[k * n + i] = f[k];
+            if (U4) U4[k * n + i] = u4[k];
+        }
+    }
+}

@@ -1,0 +1,145 @@
+"""Pins of the oracle's implicit radiation-matter step (Sec. 3.3).
+
+  * static gas (v = 0, B = 0, F_r = 0): the step reduces to the scalar equation
+    E (1 + k) = E* + k a_R T^4 with T = (gamma-1)(tau_t - E)/rho, k = h rho kappa,
+    solved here by bisection to machine precision, from weakly coupled to the
+    stiff limit where E -> a_R T^4 at fixed total energy;
+  * the matrix C^(m) of Sec. 3.3 step 2 reproduces the residual built from
+    Eqs. g0/gi when matter and Eddington tensor are frozen (sign of C_{i+1,j+1});
+  * for general states the result conserves D, B, tau_e + E_r, S + F_r exactly,
+    is consistent with con2prim, and zeroes X - X* + h G(X, V(X)) with the
+    four-force pinned by Lorentz covariance in test_oracle_physics;
+  * Picard (paper) and Newton agree where Picard converges.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from test_oracle_physics import random_states
+
+
+def _static_reference(rho, p, E0, k, a, g):
+    taut = p / (g - 1) + E0
+
+    def res(E):
+        T = (g - 1) * (taut - E) / rho
+        return E * (1 + k) - E0 - k * a * T ** 4
+
+    lo, hi = 0.0, taut
+    for _ in range(400):
+        mid = 0.5 * (lo + hi)
+        if res(mid) > 0:
+            hi = mid
+        else:
+            lo = mid
+    E = 0.5 * (lo + hi)
+    return E, (g - 1) * (taut - E)
+
+
+@pytest.mark.parametrize("k", [1e-4, 1e-1, 10.0, 1e3, 1e6])
+@pytest.mark.parametrize("case", ["cold_gas_hot_radiation", "hot_gas_cold_radiation"])
+def test_static_closed_form(k, case):
+    g = 5 / 3
+    a = 1.0
+    rho, p, E0 = (2.0, 0.01, 3.0) if case == "cold_gas_hot_radiation" else (0.5, 2.0, 1e-3)
+    P = O.Params(gamma=g, a_rad=a)
+    V = np.array([rho, 0, 0, 0, p, 0, 0, 0, E0, 0, 0, 0])
+    Us = O.prim2con(V, P)
+    kappa, hdt = 1.0, k / rho
+    U, Vn, st = O.implicit(Us, kappa, 0.7, hdt, P, Zguess=O.prim_Z(V, P))
+    assert st == 0
+    E, pe = _static_reference(rho, p, E0, k, a, g)
+    assert U[8] == pytest.approx(E, rel=1e-12)
+    assert Vn[4] == pytest.approx(pe, rel=1e-10, abs=1e-14 * (p / (g - 1) + E0))
+    np.testing.assert_array_equal(U[9:], 0.0)
+    np.testing.assert_array_equal(Vn[1:4], 0.0)
+    # approach to equilibrium: E - a_R T^4 = (E* - a_R T^4)/(1 + k)
+    aT4 = a * (Vn[4] / Vn[0]) ** 4
+    assert abs(U[8] - aT4) <= 1.000001 * abs(E0 - aT4) / (1 + k) + 1e-12 * (E0 + aT4)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_picard_matrix_reproduces_four_force(seed):
+    rng = np.random.default_rng(seed)
+    for _ in range(20):
+        kappa, sigma = 10 ** rng.uniform(-2, 2), 10 ** rng.uniform(-2, 2)
+        hdt, rho = 10 ** rng.uniform(-3, 0), 10 ** rng.uniform(-2, 1)
+        u = rng.normal(size=3) * rng.uniform(0, 2)
+        W = np.sqrt(1 + u @ u)
+        BP = 10 ** rng.uniform(-2, 1)
+        El = 10 ** rng.uniform(-1, 1)
+        n = rng.normal(size=3)
+        Fl = rng.uniform(0, 0.9) * El * n / np.linalg.norm(n)
+        Dr = O.m1_pressure(El, Fl) / El
+        Xs = np.array([1.3, 0.2, -0.1, 0.3])
+        X = np.array([0.9, -0.3, 0.2, 0.1])
+        Cm, rhs = O.picard_matrix(kappa, sigma, hdt, rho, u, W, BP, Dr, Xs)
+        G = O.four_force(kappa, sigma, rho, u, W, BP, X[0], X[1:], Dr * X[0])
+        R = X - Xs + hdt * G
+        scale = 1 + hdt * rho * (kappa + sigma) * (W ** 3) * (1 + BP)
+        np.testing.assert_allclose(Cm @ X - rhs, R, rtol=0, atol=1e-13 * scale)
+
+
+def _c1_cells(n, seed):
+    rng = np.random.default_rng(seed)
+    V = random_states(n, seed)
+    kappa = 10 ** rng.uniform(-3, 3, n)
+    sigma = 10 ** rng.uniform(-3, 2, n)
+    return V, kappa, sigma
+
+
+@pytest.mark.parametrize("hdt", [1e-4, 1e-3, 1e-2])
+def test_general_solution_conserves_and_solves(hdt):
+    g = 4 / 3
+    P = O.Params(gamma=g, a_rad=1.0)
+    V, kappa, sigma = _c1_cells(400, 7)
+    Us = O.prim2con(V, P)
+    U, Vn, st = O.implicit(Us, kappa, sigma, hdt, P, Zguess=O.prim_Z(V, P))
+    assert (st == 0).all(), np.where(st != 0)
+    np.testing.assert_array_equal(U[0], Us[0])
+    np.testing.assert_array_equal(U[5:8], Us[5:8])
+    tot = np.abs(Us[4]) + Us[8]
+    assert np.all(np.abs((U[4] + U[8]) - (Us[4] + Us[8])) <= 4e-16 * tot)
+    assert np.all(np.abs((U[1:4] + U[9:12]) - (Us[1:4] + Us[9:12])) <= 4e-16 * (tot + Us[0]))
+    Up = O.prim2con(Vn, P)
+    assert np.max(np.abs(Up - U)[:5] / (np.abs(U[4]) + U[0] + U[8])) < 1e-12
+    for i in range(U.shape[1]):
+        v = Vn[1:4, i]
+        W = 1 / np.sqrt(1 - v @ v)
+        u = W * v
+        T = Vn[4, i] / Vn[0, i]
+        X = U[8:12, i]
+        G = O.four_force(kappa[i], sigma[i], Vn[0, i], u, W, T ** 4, X[0], X[1:],
+                         O.m1_pressure(X[0], X[1:]))
+        R = X - Us[8:12, i] + hdt * G
+        scale = Us[8, i] + X[0] + hdt * np.abs(G).max()
+        assert np.abs(R).max() <= 1e-10 * scale, (i, R, scale)
+    assert np.all(np.sqrt((U[9:12] ** 2).sum(0)) <= U[8] * (1 + 1e-12))
+
+
+def test_picard_agrees_with_newton_when_it_converges():
+    g = 4 / 3
+    Pn = O.Params(gamma=g, a_rad=1e-4)
+    Pp = O.Params(gamma=g, a_rad=1e-4, implicit="picard", imp_maxit=400)
+    rng = np.random.default_rng(11)
+    V = random_states(100, 11, wmax=2.0)
+    kappa = 10 ** rng.uniform(-2, 0, 100)
+    sigma = 10 ** rng.uniform(-2, 0, 100)
+    Us = O.prim2con(V, Pn)
+    Un, _, sn = O.implicit(Us, kappa, sigma, 1e-3, Pn, Zguess=O.prim_Z(V, Pn))
+    Up, _, sp = O.implicit(Us, kappa, sigma, 1e-3, Pp, Zguess=O.prim_Z(V, Pn))
+    assert (sn == 0).all() and (sp == 0).all()
+    scale = np.abs(Us[4]) + Us[0] + Us[8]
+    assert np.max(np.abs(Un - Up) / scale) < 1e-11
+
+
+def test_picard_diverges_where_newton_converges():
+    """The paper's lagged iteration fails once 4 a_R T^3 h kappa (gamma-1)/rho >> 1
+    (hot gas, cold radiation, strong absorption); the Newton reading converges."""
+    g = 4 / 3
+    V = np.array([0.01, 0, 0, 0, 10.0, 0, 0, 0, 1e-3, 0, 0, 0])
+    for mode, ok in (("newton", True), ("picard", False)):
+        P = O.Params(gamma=g, a_rad=1.0, implicit=mode)
+        Us = O.prim2con(V, P)
+        _, _, st = O.implicit(Us, 1e3, 0.0, 1e-3, P, Zguess=O.prim_Z(V, P))
+        assert (st == 0) == ok
