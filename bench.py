@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark: zone-updates/s of the IMEX-RK3 step of the radiation-RMHD path.
+
+Workload (default): a batch of 4096 independent 1D RRMHD Riemann problems from
+seed 2212003701 (grid sizes U{128..2048}, log-uniform densities, pressures,
+radiation energies and opacities, Lorentz factors up to 10, gamma 4/3), all
+advanced together, FP64.  One "step" is one IMEX-RK3 step of every live
+instance (3 stages x {PLM + PVM-int-8 fluxes, flux difference + RK, implicit
+radiation-matter solve}); a zone-update is one cell advanced by one step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is device throughput with the state resident
+in HBM; ``e2e`` the same metric through the C-ABI host-buffer entry
+(rrmhd_imex_step_host: H2D of the state, the step, D2H of the primitives, every
+step).  N > 1 (torchrun): every rank advances its own batch (seed + rank):
+independent problems, no data-path collective, weak scaling.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP64-pipe instructions (DADD + DMUL + DFMA, thread level, ncu
+# smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum) per zone-update
+# of each launch group on this workload; measured once with ncu on a 512-instance
+# sample of the same distribution (profiles/c1_fp64_kernels.md).  0 = not yet measured.
+FP64_INST_PER_ZONE = {"faces": 0.0, "cells": 0.0}
+# Nominal FP64 rate of GB300: 1.25 TFLOP/s = 6.25e11 FP64-pipe instructions/s
+# (2 per SM per clock on 152 SMs at 2.07 GHz); no MEASURED_PEAKS entry exists for FP64.
+FP64_PEAK_INST = 6.25e11
+BYTES_PER_ZONE_STEP = 1392.0  # minimum HBM bytes per zone-update (state in/out per stage)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--instances", type=int, default=4096)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=256, help="instances in the CPU sample")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+_WORKER = {}
+
+
+def _worker_init(seed, n_inst):
+    """Pool initializer: build the oracle and the workload once per worker process."""
+    import oracle as O
+    from paper_2212_00370_gb300 import workloads as W
+    O.lib()
+    _WORKER["w"] = W.riemann_batch(n_inst, seed=seed)
+
+
+def _oracle_instance_steps(args):
+    """Worker: advance one instance by nsteps with the oracle; returns zone-updates done."""
+    idx, nsteps = args
+    import oracle as O
+    w = _WORKER["w"]
+    g, V, kappa, sigma = w.instance(idx)
+    P = O.Params(gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl)
+    V = np.ascontiguousarray(V).copy()
+    U = O.prim2con(V, P)
+    grid = O.Grid(1, (g["n"][0],), (g["dx"][0],))
+    t, steps, nfail = O.run(grid, 0.0, np.inf, U, V, kappa, sigma, P, max_steps=nsteps)
+    return g["n"][0] * steps if not nfail else 0
+
+
+def make_pool(cores, seed, n_inst):
+    pool = mp.get_context("spawn").Pool(cores, initializer=_worker_init, initargs=(seed, n_inst))
+    pool.map(_noop, range(cores))  # wait until every worker is initialised
+    return pool
+
+
+def _noop(x):
+    return x
+
+
+def cpu_oracle(pool, cores, seed, n_inst, sample, nsteps):
+    """Oracle throughput on `sample` instances (evenly spread over the batch), `nsteps`
+    steps each, over `cores` worker processes.  Returns (zone-updates/s, wall s, zones)."""
+    idx = np.linspace(0, n_inst - 1, sample).astype(int)
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_instance_steps, [(int(i), nsteps) for i in idx], chunksize=1)
+    wall = time.perf_counter() - t0
+    zones = sum(res)
+    return zones / wall, wall, zones
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(a, rank, world, pool, cores):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2212_00370_gb300 import rrmhd
+    from paper_2212_00370_gb300 import workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    seed = W.SEED_BASE + 1 + rank
+    w = W.riemann_batch(a.instances, seed=seed)
+    grids = [rrmhd.make_grid(1, g["n"], g["dx"], g["bc"]) for g in w.grids]
+    ctx = rrmhd.Context(grids, gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl)
+    ctx.set_opacity(torch.tensor(w.kappa, device="cuda"), torch.tensor(w.sigma, device="cuda"))
+    V0 = torch.tensor(w.V, device="cuda")
+    ctx.set_state(V0)
+    ctx.set_times(np.zeros(w.n_inst), np.full(w.n_inst, np.inf))
+    n_cells = np.array([g["n"][0] for g in w.grids], dtype=np.int64)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up (builds both step graphs)
+    ctx.imex_step(max(a.warmup, 2))
+    torch.cuda.synchronize()
+    st_before = ctx.inst_status()
+
+    # timed region: K graph launches, per-step events on the launching stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for k in range(a.steps):
+            ctx.imex_step(1)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(a.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    st_after = ctx.inst_status()
+    live = (st_before == 0) & (st_after == 0)
+    zones = float(n_cells[live].sum()) * a.steps
+    t_s = total_ms / 1e3
+    if world > 1:
+        tt = torch.tensor([t_s, zones], dtype=torch.float64)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_s, zones = float(mx[0]), float(tt[1])
+    value = zones / t_s
+
+    # per-launch-group device times of one more step (same kernels, no graph)
+    prof = np.zeros(4)
+    nprof = 2
+    for _ in range(nprof):
+        prof += ctx.profile_step()
+    prof /= nprof
+    zones_step = float(n_cells[live].sum())
+    groups = {"faces": prof[0] / 3.0, "cells": prof[1] / 3.0}   # ms per launch
+    dom = max(groups, key=groups.get)
+    per_zone = FP64_INST_PER_ZONE[dom]
+    # per launch: (instructions per zone-update of this group) x zone-updates / 3 launches
+    achieved = per_zone * zones_step / 3.0 / (groups[dom] / 1e3) if per_zone else None
+    roofline = {
+        "bound": "alu", "kernel": "k_" + dom + " (FP64)",
+        "achieved": achieved, "peak": FP64_PEAK_INST, "unit": "FP64-pipe inst/s",
+        "frac": (achieved / FP64_PEAK_INST) if achieved else None,
+        "traffic": None,
+        "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe; no measured FP64 peak)",
+        "launch_ms": {k: round(v, 4) for k, v in groups.items()},
+        "hbm_frac": BYTES_PER_ZONE_STEP * value / (6791.7e9),
+    }
+
+    # end-to-end through the host-buffer C-ABI entry (pinned host memory)
+    e2e = None
+    if not a.no_e2e:
+        _, Vdev = ctx.get_state()
+        h_in = torch.empty(Vdev.shape, dtype=torch.float64, pin_memory=True)
+        h_out = torch.empty(Vdev.shape, dtype=torch.float64, pin_memory=True)
+        h_in.copy_(Vdev)
+        torch.cuda.synchronize()
+        ctx.imex_step_host(h_in, h_out, 1)  # warm
+        ke = max(1, min(a.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            ctx.imex_step_host(h_in, h_out, 1)
+            h_in, h_out = h_out, h_in
+        te = time.perf_counter() - t0
+        st_e = ctx.inst_status()
+        zl = float(n_cells[st_e == 0].sum()) * ke
+        nbytes = 12 * 8 * w.ncells
+        e2e = {"value": zl / te, "unit": "zone-updates/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": ke}
+
+    out = {
+        "metric": "zone-updates/s per IMEX step (FP64; % HBM roofline; p50/p99 step time)",
+        "value": value, "unit": "zone-updates/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "C1: %d independent 1D RRMHD Riemann problems per GPU, N~U{128..2048}, "
+                               "seed 2212003701+rank, gamma 4/3, PVM-int-8 + VanLeer + IMEX-RK3, FP64"
+                               % a.instances,
+                   "instances": a.instances, "cells": int(n_cells.sum()),
+                   "live_instances": int(live.sum()), "failed_instances": int((~live).sum()),
+                   "parallelism": "replicas (independent problems per GPU)",
+                   "l2": "state %.0f MB per copy > 129 MB L2 (inputs larger than L2)" % (12 * 8 * w.ncells / 1e6)},
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": ctx.launches_per_step() * a.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and pool is not None:
+        zps, wall, zc = cpu_oracle(pool, cores, seed, a.instances, a.cpu_sample, 1)
+        out["cpu_baseline"] = {"value": zps, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
+                               "sample": "%d of the %d instances (evenly spaced), 1 step each, %d zone-updates, %.1f s wall"
+                                         % (a.cpu_sample, a.instances, zc, wall)}
+    ctx.close()
+    return out
+
+
+def run_reference(a, rank, pool, cores):
+    from paper_2212_00370_gb300 import workloads as W
+    seed = W.SEED_BASE + 1
+    for _ in range(a.warmup):
+        cpu_oracle(pool, cores, seed, a.instances, max(cores, 8), 1)
+    vals = []
+    t0 = time.perf_counter()
+    zones = 0
+    for _ in range(a.steps):
+        zps, wall, zc = cpu_oracle(pool, cores, seed, a.instances, a.cpu_sample, 1)
+        vals.append(wall)
+        zones += zc
+    wall = time.perf_counter() - t0
+    value = zones / wall
+    return {
+        "impl": "reference",
+        "metric": "zone-updates/s per IMEX step (FP64; % HBM roofline; p50/p99 step time)",
+        "value": value, "unit": "zone-updates/s", "n_gpus": 0, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * wall / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "C1: %d independent 1D RRMHD Riemann problems, FP64 CPU oracle; each step "
+                               "is a sample of %d instances" % (a.instances, a.cpu_sample),
+                   "instances": a.instances},
+        "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d instances per step, 1 IMEX step each" % a.cpu_sample},
+        "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "p50_ms": float(np.percentile(vals, 50) * 1e3), "p99_ms": float(np.percentile(vals, 99) * 1e3),
+    }
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    from oracle import build as OB
+    OB.build()
+    pool = None
+    # the oracle pool is started (spawn) before the first GPU call, on rank 0 only
+    if rank == 0 and (a.impl == "reference" or not a.no_cpu):
+        from paper_2212_00370_gb300 import workloads as W
+        pool = make_pool(cores, W.SEED_BASE + 1, a.instances)
+    try:
+        if a.impl == "reference":
+            if rank != 0:
+                return
+            out = run_reference(a, rank, pool, cores)
+        else:
+            if world > 1:
+                import torch.distributed as dist
+                dist.init_process_group("gloo")
+            from paper_2212_00370_gb300 import build as B
+            if rank == 0:
+                B.build()
+            if world > 1:
+                import torch.distributed as dist
+                dist.barrier()
+            out = run_ours(a, rank, world, pool, cores)
+            if rank != 0:
+                return
+        print(json.dumps(out), flush=True)
+    finally:
+        if pool is not None:
+            pool.close()
+            pool.join()
+
+
+if __name__ == "__main__":
+    main()

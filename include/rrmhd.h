@@ -1,0 +1,194 @@
+/*
+ * rrmhd.h -- C ABI of the GB300 (sm_103a) finite-volume IMEX update of gray-M1
+ * relativistic radiation magnetohydrodynamics with the PVM-int-8 Jacobian-free
+ * Riemann solver (Lopez-Miralles, Marti & Perucho 2022, arXiv:2212.00370).
+ *
+ * The system (Sec. 2.1, Eq. eq0) is  d_t U + d_i F^i = S  with twelve
+ * conserved variables (Eq. eqU) and primitives, both structure-of-arrays:
+ *   U = (D, S^x, S^y, S^z, tau_e, B^x, B^y, B^z, E_r, F_r^x, F_r^y, F_r^z)
+ *   V = (rho, v^x, v^y, v^z, p, B^x, B^y, B^z, E_r, F_r^x, F_r^y, F_r^z)
+ * in code units c = 1, T = p/rho, 4 pi B = a_R T^4 (Sec. 2.1).
+ *
+ * A context holds a BATCH of independent instances (a single problem is a batch
+ * of one).  Each instance is a 1D, 2D or 3D Cartesian grid with its own cell
+ * sizes, boundaries, opacities, time, end time and time step.  Fields of all
+ * instances are packed: instance i owns cells [off[i], off[i+1]) of every
+ * plane (rrmhd_cell_offsets), each grid row-major with x fastest, and a field
+ * of the context is double[12][ncells] (plane k at k*ncells).
+ *
+ * Conventions for every entry point:
+ *  - Pointers are DEVICE pointers (CUDA global memory) unless marked "host".
+ *    The caller owns them; the library never frees or retains them.
+ *  - Work is enqueued on the CUDA stream given to rrmhd_create and is
+ *    asynchronous unless the function returns host data.
+ *  - Errors are returned as rrmhd_status, never by trap or exception; the text
+ *    of the last error is available from rrmhd_last_error.  Argument errors
+ *    return RRMHD_EINVAL before any work is enqueued.  Per-cell numerical
+ *    failures (no con2prim root, no implicit solution) freeze the instance they
+ *    occur in and are reported per instance by rrmhd_get_inst_status.
+ *  - FP64 arithmetic follows one fixed IEEE operation order (no fused
+ *    multiply-add), so results are reproducible bit for bit.
+ */
+#ifndef RRMHD_H
+#define RRMHD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RRMHD_OK = 0,
+    RRMHD_EC2P = 1,       /* con2prim found no admissible root                  */
+    RRMHD_EIMPLICIT = 2,  /* implicit radiation-matter solve did not converge   */
+    RRMHD_EUNPHYS = 3,    /* inadmissible state (D <= 0, E_r <= 0, NaN speeds)  */
+    RRMHD_EINVAL = 10,    /* invalid argument                                   */
+    RRMHD_ENOMEM = 11,    /* device allocation failed                           */
+    RRMHD_ECUDA = 12      /* CUDA runtime error                                 */
+} rrmhd_status;
+
+enum { RRMHD_RECON_GODUNOV = 0, RRMHD_RECON_MINMOD = 1, RRMHD_RECON_MC = 2, RRMHD_RECON_VANLEER = 3 };
+enum { RRMHD_BC_OUTFLOW = 0, RRMHD_BC_PERIODIC = 1 };
+enum { RRMHD_FP64 = 0, RRMHD_FP32_BULK = 1 };
+
+/* One instance's grid.  Unused directions: n = 1, dx = 1.  bc applies to both
+ * sides of a direction: outflow copies the edge cell into the two ghost layers
+ * that PLM needs, periodic wraps (Sec. 4 test set-ups). */
+typedef struct {
+    int    ndim;   /* 1, 2 or 3                    */
+    int    n[3];   /* cells per direction (>= 1)   */
+    double dx[3];  /* cell size per direction (> 0) */
+    int    bc[3];  /* RRMHD_BC_* per direction     */
+} rrmhd_grid;
+
+/* Scheme options shared by all instances of a context. */
+typedef struct {
+    double gamma;      /* ideal-gas adiabatic index, Eq. eos (> 1)                       */
+    double a_rad;      /* radiation constant a_R, 4 pi B = a_R T^4 (>= 0)                 */
+    double cfl;        /* Courant number of dt = cfl / max sum_d lambda_d/dx_d            */
+    double pvm_eps;    /* epsilon of the nested flux differences, Sec. 3.2.2 (1e-8)        */
+    int    recon;      /* RRMHD_RECON_* (Sec. 3.2); VanLeer is the paper's default         */
+    int    beta_mode;  /* 1: beta = min(1/tau_L, 1/tau_R, 1) (Eq. beta); 0: beta = 1        */
+    int    precision;  /* RRMHD_FP64 (reproducible) or RRMHD_FP32_BULK                     */
+    int    c2p_maxit;  /* Newton iterations allowed in con2prim (60)                       */
+    int    imp_maxit;  /* iterations allowed in one implicit Newton solve (50)             */
+    double imp_tol;    /* implicit convergence: full Newton step <= imp_tol * E_r (1e-12)  */
+} rrmhd_opts;
+
+typedef struct rrmhd_ctx rrmhd_ctx;
+
+/* Fills o with the paper's defaults (gamma 5/3, a_R 1, CFL 0.4, eps 1e-8, VanLeer,
+ * beta on, FP64).  o: host. */
+void rrmhd_default_opts(rrmhd_opts* o);
+
+/* Creates a context for n_inst instances (grids: host array of n_inst) on the
+ * given CUDA stream (cudaStream_t, NULL = legacy default stream) of the current
+ * device, and allocates its device state.  Opacities default to 0, times to
+ * t = 0, t_end = +inf.  The problem statement is Sec. 2 (Eqs. eq0-xi).
+ * Returns EINVAL for bad grids/options, ENOMEM if allocation fails. */
+rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts* opts,
+                          void* cuda_stream, rrmhd_ctx** out);
+
+/* Releases the context and its device memory (synchronises its stream). */
+void rrmhd_destroy(rrmhd_ctx* ctx);
+
+/* Number of instances / cells of all instances / faces normal to dir (0..2). */
+int     rrmhd_num_instances(const rrmhd_ctx* ctx);
+int64_t rrmhd_num_cells(const rrmhd_ctx* ctx);
+int64_t rrmhd_num_faces(const rrmhd_ctx* ctx, int dir);
+
+/* Cell offsets of the packed layout: off (host, n_inst+1). */
+rrmhd_status rrmhd_cell_offsets(const rrmhd_ctx* ctx, int64_t* off);
+
+/* Face offsets of direction dir: instance i owns faces [off[i], off[i+1]) of a
+ * flux array of that direction, each block row-major over (n + e_dir). off: host,
+ * n_inst+1. */
+rrmhd_status rrmhd_face_offsets(const rrmhd_ctx* ctx, int dir, int64_t* off);
+
+/* Absorption kappa and scattering sigma_s (comoving, per unit mass; Eqs. g0, gi)
+ * per cell: kappa, sigma: double[ncells].  Copied into the context. */
+rrmhd_status rrmhd_set_opacity(rrmhd_ctx* ctx, const double* kappa, const double* sigma);
+
+/* Sets the state from primitives V: double[12][ncells] (copied); computes U by
+ * Eq. eqU and the CFL signal speeds. */
+rrmhd_status rrmhd_set_state(rrmhd_ctx* ctx, const double* V);
+
+/* Copies the current conserved (U) and/or primitive (V) state out:
+ * double[12][ncells] each; either may be NULL. */
+rrmhd_status rrmhd_get_state(const rrmhd_ctx* ctx, double* U, double* V);
+
+/* Per-instance current time and end time (host, n_inst each); an instance
+ * stops once t reaches t_end (the last step is clipped to land on it). */
+rrmhd_status rrmhd_set_times(rrmhd_ctx* ctx, const double* t, const double* t_end);
+
+/* Per-instance time and the size of the last step taken (host, n_inst each;
+ * either may be NULL).  Synchronises the stream. */
+rrmhd_status rrmhd_get_times(const rrmhd_ctx* ctx, double* t, double* dt_last);
+
+/* Per-instance status (host int32[n_inst]): 0 ok, else the rrmhd_status of the
+ * first cell failure.  Failed instances are frozen.  Synchronises the stream. */
+rrmhd_status rrmhd_get_inst_status(const rrmhd_ctx* ctx, int32_t* status);
+
+/* Advances every live instance by nsteps IMEX-RK3 steps (Sec. 3.1): each
+ * step takes dt = cfl / max sum_d lambda_d/dx_d (clipped to t_end) and runs
+ * three stages of {PLM + PVM-int-8 flux at every face (Sec. 3.2), flux
+ * difference and RK combination (Eq. explicit), implicit radiation-matter solve
+ * (Sec. 3.3)} with implicit weights 1, 1/4, 2/3.  Enqueued as one CUDA graph
+ * per step; returns without synchronising. */
+rrmhd_status rrmhd_imex_step(rrmhd_ctx* ctx, int nsteps);
+
+/* Same as rrmhd_imex_step, from and to HOST buffers: copies V_in (host
+ * double[12][ncells], pinned memory recommended) to the device, sets it as the
+ * state, takes nsteps steps and copies the primitives back to V_out (host).
+ * Synchronous. */
+rrmhd_status rrmhd_imex_step_host(rrmhd_ctx* ctx, const double* V_in, double* V_out, int nsteps);
+
+/* Pointwise Eq. eqU on caller buffers: V, U double[12][n]. */
+rrmhd_status rrmhd_prim2con(rrmhd_ctx* ctx, const double* V, double* U, int64_t n);
+
+/* Pointwise con2prim (the inversion Sec. 3.2.2 step 2 refers to; Newton-Raphson
+ * of Mignone & McKinney 2007 in W' = rho h W^2 - D): U double[12][n] -> V
+ * double[12][n]; Zguess double[n] (rho h W^2 warm start) or NULL; status
+ * int32[n] (0 ok, RRMHD_EC2P, RRMHD_EUNPHYS) or NULL.  V is zero where it fails. */
+rrmhd_status rrmhd_con2prim(rrmhd_ctx* ctx, const double* U, const double* Zguess, double* V,
+                            int32_t* status, int64_t n);
+
+/* Numerical flux (Eqs. generalflux, beta; Sec. 3.2.2 steps 1-7) at every face
+ * normal to dir of every instance, from the context's current primitives:
+ * PLM reconstruction with the Godunov fallback (Sec. 3.2), then
+ * F^ = (F_L + F_R)/2 - beta p_3(A) (U_R - U_L)/2 with p_3 the degree-8 internal
+ * approximation of |x| (Eq. iterat), A^2 products by nested flux differences.
+ * Fhat: double[12][num_faces(dir)] laid out as rrmhd_face_offsets(dir). */
+rrmhd_status rrmhd_flux_sweep(rrmhd_ctx* ctx, int dir, double* Fhat);
+
+/* Implicit radiation-matter step of every cell (Sec. 3.3, Eqs. timeadv, totale,
+ * totalm): solves E_r = E* - h G^0, F_r = F* - h G^i (Eqs. g0, gi) with
+ * tau_e + E_r and S + F_r conserved and the matter recovered by con2prim.
+ * hdt: the implicit weight times dt.  Ustar: double[12][ncells] (U*);
+ * Zguess: double[ncells] warm start or NULL; opacities from the context.
+ * U, V: double[12][ncells] results; status: int32[ncells] or NULL. */
+rrmhd_status rrmhd_implicit_source(rrmhd_ctx* ctx, double hdt, const double* Ustar,
+                                   const double* Zguess, double* U, double* V, int32_t* status);
+
+/* One IMEX-RK3 step exactly as rrmhd_imex_step takes it, but launched without
+ * the CUDA graph and with CUDA events recorded on the context's stream between
+ * launch groups; synchronises.  ms (host, 4): total device time of
+ * [0] the 3 face-flux launches, [1] the 3 cell-update launches,
+ * [2] the 6 admissibility-fallback launches, [3] the 2 per-instance
+ * time-step launches. */
+rrmhd_status rrmhd_profile_step(rrmhd_ctx* ctx, double* ms);
+
+/* Kernel launches one rrmhd_imex_step step enqueues (for launch accounting). */
+int rrmhd_launches_per_step(const rrmhd_ctx* ctx);
+
+/* rho h W^2 of primitives: V double[12][n] -> Z double[n] (con2prim warm starts). */
+rrmhd_status rrmhd_prim_z(rrmhd_ctx* ctx, const double* V, double* Z, int64_t n);
+
+/* Text of the last error of this context (static storage owned by ctx). */
+const char* rrmhd_last_error(const rrmhd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -40,7 +40,7 @@ class _Params(C.Structure):
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "c2p_calls", "c2p_iters", "c2p_fail", "flux_evals", "pvm_faces", "pvm_fallback",
-        "imp_cells", "imp_iters", "imp_resid", "imp_jac", "imp_fail")]
+        "imp_cells", "imp_iters", "imp_resid", "imp_jac", "imp_fail", "fallback_cells")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -118,6 +118,7 @@ def lib():
             "or_picard_matrix": (None, [C.c_double, C.c_double, C.c_double, C.c_double, dp,
                                         C.c_double, C.c_double, dp, dp, dp, dp]),
             "or_solve4": (C.c_int, [dp, dp, dp]),
+            "or_llf_flux": (None, [P, C.c_int, dp, dp, dp]),
             "or_grid_dt": (C.c_double, [P, G, dp]),
             "or_grid_face_flux": (C.c_int, [P, G, C.c_int, dp, dp, dp, dp, dp, S]),
             "or_grid_stage": (C.c_int, [P, G, C.c_int, C.c_double, dp, dp, dp, dp, dp, dp, dp,
@@ -273,6 +274,14 @@ def picard_matrix(kappa, sigma, hdt, rho, u, W, BP, Dr, Xs):
     rhs = np.empty(4)
     lib().or_picard_matrix(kappa, sigma, hdt, rho, _d(u), W, BP, _d(Dr), _d(Xs), _d(Cm), _d(rhs))
     return Cm, rhs
+
+
+def llf_flux(VL, VR, d, P):
+    VL = np.ascontiguousarray(VL, dtype=np.float64)
+    VR = np.ascontiguousarray(VR, dtype=np.float64)
+    F = np.empty(12)
+    lib().or_llf_flux(C.byref(P.struct()), d, _d(VL), _d(VR), _d(F))
+    return F
 
 
 def solve4(A, b):

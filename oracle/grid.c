@@ -41,13 +41,16 @@ double or_grid_dt(const or_params* P, const or_grid* g, const double* V)
 {
     int64_t N = ncells(g);
     double smax = 0.0;
+    int bad = 0;
     for (int64_t c = 0; c < N; c++) {
         double v[12];
         load(V, N, c, v);
         double s = or_signal_speed(P, 0, v) / g->dx[0];
         for (int d = 1; d < g->ndim; d++) s = s + or_signal_speed(P, d, v) / g->dx[d];
+        if (s != s) bad = 1;   /* NaN speed: inadmissible cell */
         if (s > smax) smax = s;
     }
+    if (bad) return NAN;
     return P->cfl / smax;
 }
 
@@ -96,66 +99,161 @@ int or_grid_face_flux(const or_params* P, const or_grid* g, int dir, const doubl
     return nfb;
 }
 
+typedef struct {
+    const or_params* P;
+    const or_grid* g;
+    int stage;
+    double dt, a, b, hdt, dtdx[3];
+    double* Fh[3];
+    int m[3][3];
+    const double *U0, *Us, *Vs, *kappa, *sigma;
+} stage_ctx;
+
+/* U* of one cell from its face fluxes, then the implicit solve (Sec. 3.3). */
+static int cell_update(const stage_ctx* s, int i, int j, int k, double Un[12], double Vn[12],
+                       or_stats* st)
+{
+    const or_grid* g = s->g;
+    int64_t N = ncells(g);
+    int64_t c = lin(g, i, j, k);
+    int64_t fl[3], fr[3], NF[3];
+    for (int d = 0; d < g->ndim; d++) {
+        int p[3] = {i, j, k};
+        NF[d] = (int64_t)s->m[d][0] * s->m[d][1] * s->m[d][2];
+        fl[d] = ((int64_t)p[2] * s->m[d][1] + p[1]) * s->m[d][0] + p[0];
+        p[d] += 1;
+        fr[d] = ((int64_t)p[2] * s->m[d][1] + p[1]) * s->m[d][0] + p[0];
+    }
+    double Ust[12], vs[12];
+    for (int q = 0; q < 12; q++) {
+        double acc = (s->Fh[0][q * NF[0] + fr[0]] - s->Fh[0][q * NF[0] + fl[0]]) * s->dtdx[0];
+        for (int d = 1; d < g->ndim; d++)
+            acc = acc + (s->Fh[d][q * NF[d] + fr[d]] - s->Fh[d][q * NF[d] + fl[d]]) * s->dtdx[d];
+        if (s->stage == 1)
+            Ust[q] = s->Us[q * N + c] - acc;
+        else
+            Ust[q] = s->a * s->U0[q * N + c] + s->b * (s->Us[q * N + c] - acc);
+    }
+    load(s->Vs, N, c, vs);
+    double Zg = or_prim_Z(s->P, vs);
+    return or_implicit(s->P, s->kappa[c], s->sigma[c], s->hdt, Ust, Zg, Un, Vn, st);
+}
+
+static int inadmissible(int rc) { return rc == OR_EC2P || rc == OR_EUNPHYS; }
+
 /* One IMEX-RK3 stage (Sec. 3.1):
  *   stage 1: U* = U^(0) + dt L(U^(0)),                         U^(1) = U* + dt S
  *   stage 2: U* = 3/4 U^(0) + 1/4 (U^(1) + dt L(U^(1))),       U^(2) = U* + dt/4 S
  *   stage 3: U* = 1/3 U^(0) + 2/3 (U^(2) + dt L(U^(2))),       U^(3) = U* + 2dt/3 S
  * with dt L = -sum_d dt/dx_d (F_{+} - F_{-}) and the source solved implicitly
- * at the new stage state. */
+ * at the new stage state.
+ * Admissibility fallback (a posteriori, conservative): cells whose U* has no
+ * con2prim root are flagged; every face adjacent to a flagged cell gets the
+ * first-order lambda_max = 1 Rusanov flux of the cell-centre states
+ * (or_llf_flux), and all cells touching such a face are updated again.  A cell
+ * that still fails counts as failed.  Uout/Vout must not alias the inputs. */
 int or_grid_stage(const or_params* P, const or_grid* g, int stage, double dt,
                   const double* U0, const double* Us, const double* Vs,
                   const double* kappa, const double* sigma,
                   double* Uout, double* Vout, int32_t* cell_status, or_stats* st)
 {
     int64_t N = ncells(g);
-    double* Fh[3] = {0, 0, 0};
-    int m[3][3];
+    stage_ctx s;
+    s.P = P;
+    s.g = g;
+    s.stage = stage;
+    s.dt = dt;
+    s.U0 = U0;
+    s.Us = Us;
+    s.Vs = Vs;
+    s.kappa = kappa;
+    s.sigma = sigma;
+    s.Fh[0] = s.Fh[1] = s.Fh[2] = 0;
     for (int d = 0; d < g->ndim; d++) {
-        face_dims(g, d, m[d]);
-        Fh[d] = (double*)malloc(sizeof(double) * 12 * (size_t)m[d][0] * m[d][1] * m[d][2]);
-        or_grid_face_flux(P, g, d, Us, Vs, kappa, sigma, Fh[d], st);
+        face_dims(g, d, s.m[d]);
+        s.Fh[d] = (double*)malloc(sizeof(double) * 12 * (size_t)s.m[d][0] * s.m[d][1] * s.m[d][2]);
+        or_grid_face_flux(P, g, d, Us, Vs, kappa, sigma, s.Fh[d], st);
     }
-    double a = 0.0, b = 1.0, w = 1.0;
-    if (stage == 2) { a = 0.75; b = 0.25; w = 0.25; }
-    if (stage == 3) { a = 1.0 / 3.0; b = 2.0 / 3.0; w = 2.0 / 3.0; }
-    double hdt = w * dt;
-    double dtdx[3];
-    for (int d = 0; d < 3; d++) dtdx[d] = dt / g->dx[d];
+    s.a = 0.0;
+    s.b = 1.0;
+    double w = 1.0;
+    if (stage == 2) { s.a = 0.75; s.b = 0.25; w = 0.25; }
+    if (stage == 3) { s.a = 1.0 / 3.0; s.b = 2.0 / 3.0; w = 2.0 / 3.0; }
+    s.hdt = w * dt;
+    for (int d = 0; d < 3; d++) s.dtdx[d] = dt / g->dx[d];
 
-    int nfail = 0;
+    unsigned char* bad = (unsigned char*)calloc((size_t)N, 1);
+    int nfail = 0, nbad = 0;
     for (int k = 0; k < g->n[2]; k++)
         for (int j = 0; j < g->n[1]; j++)
             for (int i = 0; i < g->n[0]; i++) {
                 int64_t c = lin(g, i, j, k);
-                int64_t fl[3], fr[3], NF[3];
-                for (int d = 0; d < g->ndim; d++) {
-                    int p[3] = {i, j, k};
-                    NF[d] = (int64_t)m[d][0] * m[d][1] * m[d][2];
-                    fl[d] = ((int64_t)p[2] * m[d][1] + p[1]) * m[d][0] + p[0];
-                    p[d] += 1;
-                    fr[d] = ((int64_t)p[2] * m[d][1] + p[1]) * m[d][0] + p[0];
-                }
-                double Ust[12], Un[12], Vn[12], vs[12];
-                for (int q = 0; q < 12; q++) {
-                    double acc = (Fh[0][q * NF[0] + fr[0]] - Fh[0][q * NF[0] + fl[0]]) * dtdx[0];
-                    for (int d = 1; d < g->ndim; d++)
-                        acc = acc + (Fh[d][q * NF[d] + fr[d]] - Fh[d][q * NF[d] + fl[d]]) * dtdx[d];
-                    if (stage == 1)
-                        Ust[q] = Us[q * N + c] - acc;
-                    else
-                        Ust[q] = a * U0[q * N + c] + b * (Us[q * N + c] - acc);
-                }
-                load(Vs, N, c, vs);
-                double Zg = or_prim_Z(P, vs);
-                int rc = or_implicit(P, kappa[c], sigma[c], hdt, Ust, Zg, Un, Vn, st);
+                double Un[12], Vn[12];
+                int rc = cell_update(&s, i, j, k, Un, Vn, st);
                 if (cell_status) cell_status[c] = rc;
-                if (rc != OR_OK) nfail++;
+                if (inadmissible(rc)) {
+                    bad[c] = 1;
+                    nbad++;
+                } else if (rc != OR_OK) {
+                    nfail++;
+                }
                 for (int q = 0; q < 12; q++) {
                     Uout[q * N + c] = Un[q];
                     Vout[q * N + c] = Vn[q];
                 }
             }
-    for (int d = 0; d < g->ndim; d++) free(Fh[d]);
+
+    if (nbad) {
+        /* Rusanov fluxes at every face next to a flagged cell */
+        for (int d = 0; d < g->ndim; d++) {
+            int64_t NF = (int64_t)s.m[d][0] * s.m[d][1] * s.m[d][2];
+            for (int k = 0; k < s.m[d][2]; k++)
+                for (int j = 0; j < s.m[d][1]; j++)
+                    for (int i = 0; i < s.m[d][0]; i++) {
+                        int pos[3] = {i, j, k}, ql[3] = {i, j, k}, qr[3] = {i, j, k};
+                        ql[d] = map_idx(pos[d] - 1, g->n[d], g->bc[d]);
+                        qr[d] = map_idx(pos[d], g->n[d], g->bc[d]);
+                        int64_t cl = lin(g, ql[0], ql[1], ql[2]), cr = lin(g, qr[0], qr[1], qr[2]);
+                        if (!bad[cl] && !bad[cr]) continue;
+                        double vl[12], vr[12], F[12];
+                        load(Vs, N, cl, vl);
+                        load(Vs, N, cr, vr);
+                        or_llf_flux(P, d, vl, vr, F);
+                        int64_t fi = ((int64_t)k * s.m[d][1] + j) * s.m[d][0] + i;
+                        for (int q = 0; q < 12; q++) s.Fh[d][q * NF + fi] = F[q];
+                    }
+        }
+        /* update again every cell with a changed face: flagged or next to one */
+        for (int k = 0; k < g->n[2]; k++)
+            for (int j = 0; j < g->n[1]; j++)
+                for (int i = 0; i < g->n[0]; i++) {
+                    int64_t c = lin(g, i, j, k);
+                    int hit = bad[c];
+                    for (int d = 0; d < g->ndim && !hit; d++)
+                        for (int e = -1; e <= 1; e += 2) {
+                            int q[3] = {i, j, k};
+                            int pd = q[d] + e;
+                            q[d] = map_idx(pd, g->n[d], g->bc[d]);
+                            /* an outflow ghost face is not shared with a neighbour */
+                            if (pd < 0 || pd >= g->n[d]) {
+                                if (g->bc[d] != OR_BC_PERIODIC) continue;
+                            }
+                            if (bad[lin(g, q[0], q[1], q[2])]) hit = 1;
+                        }
+                    if (!hit) continue;
+                    if (st) st->fallback_cells++;
+                    double Un[12], Vn[12];
+                    int rc = cell_update(&s, i, j, k, Un, Vn, st);
+                    if (cell_status) cell_status[c] = rc;
+                    if (rc != OR_OK) nfail++;
+                    for (int q = 0; q < 12; q++) {
+                        Uout[q * N + c] = Un[q];
+                        Vout[q * N + c] = Vn[q];
+                    }
+                }
+    }
+    free(bad);
+    for (int d = 0; d < g->ndim; d++) free(s.Fh[d]);
     return nfail;
 }
 
@@ -172,7 +270,11 @@ int or_grid_step(const or_params* P, const or_grid* g, double dt, double* U, dou
     int nfail = 0;
     nfail += or_grid_stage(P, g, 1, dt, U, U, V, kappa, sigma, U1, V1, 0, st);
     if (!nfail) nfail += or_grid_stage(P, g, 2, dt, U, U1, V1, kappa, sigma, U2, V2, 0, st);
-    if (!nfail) nfail += or_grid_stage(P, g, 3, dt, U, U2, V2, kappa, sigma, U, V, 0, st);
+    if (!nfail) nfail += or_grid_stage(P, g, 3, dt, U, U2, V2, kappa, sigma, U1, V1, 0, st);
+    if (!nfail) {
+        memcpy(U, U1, bytes);
+        memcpy(V, V1, bytes);
+    }
     free(U1);
     free(V1);
     free(U2);
@@ -191,6 +293,10 @@ int or_grid_run(const or_params* P, const or_grid* g, double t0, double t_end, i
     while (t < t_end && s < max_steps) {
         double dt = or_grid_dt(P, g, V);
         if (t + dt > t_end) dt = t_end - t;
+        if (!(dt > 0.0)) {   /* NaN or non-positive: no admissible step */
+            nfail = 1;
+            break;
+        }
         nfail = or_grid_step(P, g, dt, U, V, kappa, sigma, st);
         if (nfail) break;
         t = t + dt;

@@ -302,8 +302,9 @@ int or_implicit(const or_params* P, double kappa, double sigma, double hdt,
     double R[4], Z = Zguess;
     int fail = imp_residual(&c, X, Zguess, R, V, &Z);
     if (fail) {
+        /* the explicit state U* itself is inadmissible (no con2prim root or E_r <= 0) */
         if (st) st->imp_fail++;
-        return OR_EIMPLICIT;
+        return OR_EC2P;
     }
     if (P->imp_mode == OR_IMP_PICARD) {
         fail = picard(&c, X, V, &Z);

@@ -62,6 +62,7 @@ typedef struct {
     int64_t c2p_calls, c2p_iters, c2p_fail;
     int64_t flux_evals, pvm_faces, pvm_fallback;
     int64_t imp_cells, imp_iters, imp_resid, imp_jac, imp_fail;
+    int64_t fallback_cells;
 } or_stats;
 
 void or_params_init(or_params* P);
@@ -84,6 +85,8 @@ void   or_reconstruct(const or_params* P, const double Vm1[12], const double V0[
                       const double Vp1[12], double Vminus[12], double Vplus[12], int* fallback);
 int    or_pvm_flux(const or_params* P, int dir, const double VL[12], const double VR[12],
                    double tauL, double tauR, double Fhat[12], double U4[12], or_stats* st);
+void   or_llf_flux(const or_params* P, int dir, const double VL[12], const double VR[12],
+                   double Fhat[12]);
 
 /* ---- implicit step (implicit.c) ---- */
 int  or_implicit(const or_params* P, double kappa, double sigma, double hdt,

@@ -147,6 +147,20 @@ int or_pvm_flux(const or_params* P, int dir, const double VL[12], const double V
     return fail;
 }
 
+/* First-order local Lax-Friedrichs (Rusanov) flux with lambda_max = 1, i.e.
+ * Q = I in Eq. generalflux, from the cell-centre states of the two cells
+ * adjacent to the face.  Used only by the admissibility fallback. */
+void or_llf_flux(const or_params* P, int dir, const double VL[12], const double VR[12],
+                 double Fhat[12])
+{
+    double UL[12], UR[12], FL[12], FR[12];
+    or_prim2con(P, VL, UL);
+    or_prim2con(P, VR, UR);
+    or_flux(P, dir, VL, UL, FL);
+    or_flux(P, dir, VR, UR, FR);
+    for (int k = 0; k < 12; k++) Fhat[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * (UR[k] - UL[k]);
+}
+
 void or_pvm_flux_n(const or_params* P, int dir, int64_t n, const double* VL, const double* VR,
                    const double* tauL, const double* tauR, double* Fhat, double* U4,
                    int32_t* status, or_stats* st)

@@ -1,0 +1,83 @@
+// batch.h -- device layout of a batch of independent instances (ragged 1D, 2D
+// and 3D grids) and the launchers of the stage kernels.  Internal to librrmhd.
+//
+// Layout (all device, structure of arrays):
+//   cells  : instance i owns cells [cell_off[i], cell_off[i+1]) of every plane,
+//            row-major with x fastest;  U, V planes are [12][ncells].
+//   faces  : direction-major; faces normal to d of instance i are
+//            [dir_base[d] + face_off[d][i], ... + nfaces(i,d)), each instance's
+//            block row-major over (n + e_d) with x fastest;  Fhat is [12][nfaces].
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "physics_f64.cuh"
+
+namespace rr {
+
+struct InstDesc {
+  int ndim;
+  int n[3];
+  int bc[3];  // 0 outflow, 1 periodic (both sides of the direction)
+  double dx[3];
+  int64_t cell_off;
+  int64_t face_off[3];  // within the direction's block
+};
+
+// Per-instance time-stepping state (device arrays of length n_inst).
+struct InstState {
+  double* t;
+  double* t_end;
+  double* dt;
+  unsigned long long* smax;  // max_cells sum_d lambda_d/dx_d, as the bits of a non-negative double
+  int* status;               // 0 ok, else the first failing Status
+};
+
+struct Batch {
+  int n_inst;
+  int64_t ncells;
+  int64_t nfaces;
+  int64_t dir_base[4];       // faces of direction d: [dir_base[d], dir_base[d+1])
+  const InstDesc* inst;      // [n_inst]
+  const int64_t* cell_off;   // [n_inst + 1]
+  const int64_t* face_off;   // [3][n_inst + 1] (prefix sums within each direction)
+  InstState st;
+};
+
+struct StageArgs {
+  Params P;
+  Batch b;
+  int stage;               // 1, 2, 3
+  const double* U0;        // U^(0) (state at the start of the step)
+  const double* V0;        // V^(0)
+  const double* Us;        // U^(s-1)
+  const double* Vs;        // V^(s-1)
+  const double* kappa;
+  const double* sigma;
+  double* Fhat;            // [12][fstride]; face g is stored at column g - out_base
+  int64_t fstride;
+  int64_t f_begin, f_end;  // face range handled by a face launch
+  int64_t out_base;
+  int check_active;        // skip instances that are finished or failed
+  double* Uout;            // must not alias U0, Us, Vs (the fallback pass re-reads them)
+  double* Vout;
+  int32_t* cell_status;    // optional per-cell status
+  uint8_t* bad;            // [ncells] cells whose U* is inadmissible (admissibility fallback)
+};
+
+// FP64 path (bit-compatible with the oracle's arithmetic order)
+void launch_faces_f64(const StageArgs& a, cudaStream_t s);
+void launch_cells_f64(const StageArgs& a, cudaStream_t s);
+void launch_fallback_f64(const StageArgs& a, cudaStream_t s);
+void launch_signal_f64(const Params& P, const Batch& b, const double* V, cudaStream_t s);
+void launch_begin_step(const Params& P, const Batch& b, cudaStream_t s);
+void launch_end_step(const Batch& b, cudaStream_t s);
+void launch_prim2con_f64(const Params& P, const double* V, double* U, int64_t n, cudaStream_t s);
+void launch_con2prim_f64(const Params& P, const double* U, const double* Zg, double* V,
+                         int32_t* status, int64_t n, cudaStream_t s);
+void launch_prim_Z_f64(const Params& P, const double* V, double* Z, int64_t n, cudaStream_t s);
+void launch_implicit_f64(const Params& P, const Batch& b, double hdt, const double* Us,
+                         const double* Zg, const double* kappa, const double* sigma, double* U,
+                         double* V, int32_t* status, cudaStream_t s);
+
+}  // namespace rr

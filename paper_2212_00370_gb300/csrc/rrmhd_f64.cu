@@ -1,0 +1,442 @@
+// rrmhd_f64.cu -- FP64 kernels of one IMEX-RK3 stage over a batch of instances
+// (arXiv:2212.00370, Secs. 3.1-3.3).  Compiled with --fmad=false: see the
+// arithmetic contract in physics_f64.cuh.
+//
+// A stage is two launches over packed work lists, so ragged batches keep every
+// lane busy:
+//   k_faces : one thread per face (all directions, all instances): stencil of
+//             4 cells along the face normal through the boundary map, PLM +
+//             fallback, PVM-int-8 flux -> Fhat.
+//   k_cells : one thread per cell: flux difference and RK combination, then
+//             the implicit radiation-matter solve -> U^(s), V^(s); stage 3 also
+//             reduces the next CFL signal speed per instance.
+// The path is FP64-pipe bound (tens of thousands of FP64 instructions per cell
+// and a few hundred bytes of traffic), so the layout favours full warps and low
+// register pressure over shared-memory staging.
+#include <cuda_runtime.h>
+
+#include "batch.h"
+#include "scheme_f64.cuh"
+
+namespace rr {
+
+namespace {
+
+constexpr int kFaceThreads = 128;
+constexpr int kCellThreads = 128;
+
+// largest i in [0, n) with off[i] <= g  (off non-decreasing, off[0] = 0)
+__device__ __forceinline__ int find_inst(const int64_t* off, int n, int64_t g) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= g)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int map_idx(int c, int n, int bc) {
+  if (bc == 1) {
+    const int m = c % n;
+    return m < 0 ? m + n : m;
+  }
+  return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+__device__ __forceinline__ void load12(const double* __restrict__ A, int64_t stride, int64_t c,
+                                       double* x) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) x[k] = __ldg(A + k * stride + c);
+}
+
+__device__ __forceinline__ bool inst_active(const Batch& b, int i) {
+  return b.st.status[i] == 0 && b.st.dt[i] > 0.0;
+}
+
+__global__ void __launch_bounds__(kFaceThreads) k_faces(StageArgs a) {
+  const int64_t g = a.f_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.f_end) return;
+  const Batch& b = a.b;
+  const int d = (g >= b.dir_base[2]) ? 2 : (g >= b.dir_base[1] ? 1 : 0);
+  const int64_t gl = g - b.dir_base[d];
+  const int64_t* off = b.face_off + (int64_t)d * (b.n_inst + 1);
+  const int i = find_inst(off, b.n_inst, gl);
+  if (a.check_active && !inst_active(b, i)) return;
+  const InstDesc I = b.inst[i];
+  const int64_t lf = gl - off[i];
+  const int m0 = I.n[0] + (d == 0);
+  const int m1 = I.n[1] + (d == 1);
+  int pos[3];
+  pos[0] = (int)(lf % m0);
+  const int64_t r = lf / m0;
+  pos[1] = (int)(r % m1);
+  pos[2] = (int)(r / m1);
+  const int f = pos[d];
+  int64_t cidx[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    int q[3] = {pos[0], pos[1], pos[2]};
+    q[d] = map_idx(f - 2 + s, I.n[d], I.bc[d]);
+    cidx[s] = I.cell_off + ((int64_t)q[2] * I.n[1] + q[1]) * I.n[0] + q[0];
+  }
+  const int64_t N = b.ncells;
+  double VL[NV], VR[NV];
+  {
+    double w0[NV], w1[NV], w2[NV], tmp[NV];
+    load12(a.Vs, N, cidx[0], w0);
+    load12(a.Vs, N, cidx[1], w1);
+    load12(a.Vs, N, cidx[2], w2);
+    reconstruct(a.P.recon, w0, w1, w2, tmp, VL);  // cell f-1: its right face
+    load12(a.Vs, N, cidx[3], w0);
+    reconstruct(a.P.recon, w1, w2, w0, VR, tmp);  // cell f: its left face
+  }
+  const double dxd = I.dx[d];
+  const double tauL = (__ldg(a.Us + cidx[1]) * (__ldg(a.kappa + cidx[1]) + __ldg(a.sigma + cidx[1]))) * dxd;
+  const double tauR = (__ldg(a.Us + cidx[2]) * (__ldg(a.kappa + cidx[2]) + __ldg(a.sigma + cidx[2]))) * dxd;
+  double F[NV];
+  pvm_flux(a.P, d, VL, VR, tauL, tauR, F);
+  const int64_t o = g - a.out_base;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) a.Fhat[k * a.fstride + o] = F[k];
+}
+
+struct CellPos {
+  int i;       // instance
+  int p[3];    // position in the instance's grid
+  InstDesc I;
+};
+
+__device__ __forceinline__ CellPos cell_pos(const Batch& b, int64_t c) {
+  CellPos q;
+  q.i = find_inst(b.cell_off, b.n_inst, c);
+  q.I = b.inst[q.i];
+  const int64_t lc = c - q.I.cell_off;
+  q.p[0] = (int)(lc % q.I.n[0]);
+  const int64_t r = lc / q.I.n[0];
+  q.p[1] = (int)(r % q.I.n[1]);
+  q.p[2] = (int)(r / q.I.n[1]);
+  return q;
+}
+
+// U* of cell c from its face fluxes (flux difference and RK combination,
+// Sec. 3.1), then the implicit solve (Sec. 3.3); returns a Status.
+__device__ __forceinline__ int cell_update(const StageArgs& a, int64_t c, const CellPos& q,
+                                           double* Un, double* Vn) {
+  const Batch& b = a.b;
+  const InstDesc& I = q.I;
+  const double dt = b.st.dt[q.i];
+  double dtdx[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dtdx[d] = dt / I.dx[d];
+  int64_t fl[3], fr[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int m0 = I.n[0] + (d == 0);
+    const int m1 = I.n[1] + (d == 1);
+    const int64_t base = b.dir_base[d] + b.face_off[(int64_t)d * (b.n_inst + 1) + q.i];
+    fl[d] = base + ((int64_t)q.p[2] * m1 + q.p[1]) * m0 + q.p[0];
+    int r[3] = {q.p[0], q.p[1], q.p[2]};
+    r[d] += 1;
+    fr[d] = base + ((int64_t)r[2] * m1 + r[1]) * m0 + r[0];
+  }
+  double ca = 0.0, cb = 1.0, cw = 1.0;
+  if (a.stage == 2) {
+    ca = 0.75;
+    cb = 0.25;
+    cw = 0.25;
+  } else if (a.stage == 3) {
+    ca = 1.0 / 3.0;
+    cb = 2.0 / 3.0;
+    cw = 2.0 / 3.0;
+  }
+  const double hdt = cw * dt;
+  const int64_t N = b.ncells;
+  const int64_t FS = a.fstride;
+  double Ust[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double acc = (a.Fhat[k * FS + fr[0]] - a.Fhat[k * FS + fl[0]]) * dtdx[0];
+    for (int d = 1; d < I.ndim; ++d)
+      acc = acc + (a.Fhat[k * FS + fr[d]] - a.Fhat[k * FS + fl[d]]) * dtdx[d];
+    const double us = a.Us[k * N + c];
+    if (a.stage == 1)
+      Ust[k] = us - acc;
+    else
+      Ust[k] = ca * a.U0[k * N + c] + cb * (us - acc);
+  }
+  double vs[NV];
+  load12(a.Vs, N, c, vs);
+  const double Zg = prim_Z(a.P, vs);
+  return implicit_cell(a.P, a.kappa[c], a.sigma[c], hdt, Ust, Zg, Un, Vn);
+}
+
+__device__ __forceinline__ void store_cell(const StageArgs& a, int64_t c, const double* Un,
+                                           const double* Vn) {
+  const int64_t N = a.b.ncells;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    a.Uout[k * N + c] = Un[k];
+    a.Vout[k * N + c] = Vn[k];
+  }
+}
+
+// Pass 1: every cell.  A cell whose U* is inadmissible is only flagged.
+__global__ void __launch_bounds__(kCellThreads) k_cells(StageArgs a) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.b.ncells) return;
+  const CellPos q = cell_pos(a.b, c);
+  if (!inst_active(a.b, q.i)) return;
+  double Un[NV], Vn[NV];
+  const int rc = cell_update(a, c, q, Un, Vn);
+  if (a.cell_status) a.cell_status[c] = rc;
+  const bool inadmissible = (rc == ST_C2P || rc == ST_UNPHYS);
+  a.bad[c] = inadmissible ? 1 : 0;
+  if (inadmissible) return;
+  if (rc != ST_OK) {
+    atomicCAS(a.b.st.status + q.i, 0, rc);
+    return;
+  }
+  store_cell(a, c, Un, Vn);
+}
+
+// Admissibility fallback, faces: first-order Rusanov flux at every face next
+// to a flagged cell.
+__global__ void __launch_bounds__(kFaceThreads) k_fallback_faces(StageArgs a) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Batch& b = a.b;
+  if (g >= b.nfaces) return;
+  const int d = (g >= b.dir_base[2]) ? 2 : (g >= b.dir_base[1] ? 1 : 0);
+  const int64_t gl = g - b.dir_base[d];
+  const int64_t* off = b.face_off + (int64_t)d * (b.n_inst + 1);
+  const int i = find_inst(off, b.n_inst, gl);
+  if (!inst_active(b, i)) return;
+  const InstDesc I = b.inst[i];
+  const int64_t lf = gl - off[i];
+  const int m0 = I.n[0] + (d == 0);
+  const int m1 = I.n[1] + (d == 1);
+  int pos[3];
+  pos[0] = (int)(lf % m0);
+  const int64_t r = lf / m0;
+  pos[1] = (int)(r % m1);
+  pos[2] = (int)(r / m1);
+  int ql[3] = {pos[0], pos[1], pos[2]}, qr[3] = {pos[0], pos[1], pos[2]};
+  ql[d] = map_idx(pos[d] - 1, I.n[d], I.bc[d]);
+  qr[d] = map_idx(pos[d], I.n[d], I.bc[d]);
+  const int64_t cl = I.cell_off + ((int64_t)ql[2] * I.n[1] + ql[1]) * I.n[0] + ql[0];
+  const int64_t cr = I.cell_off + ((int64_t)qr[2] * I.n[1] + qr[1]) * I.n[0] + qr[0];
+  if (!a.bad[cl] && !a.bad[cr]) return;
+  double vl[NV], vr[NV], F[NV];
+  load12(a.Vs, b.ncells, cl, vl);
+  load12(a.Vs, b.ncells, cr, vr);
+  llf_flux(a.P, d, vl, vr, F);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) a.Fhat[k * a.fstride + g] = F[k];
+}
+
+// Admissibility fallback, cells: update again every cell with a changed face
+// (flagged, or sharing a face with a flagged cell); stage 3 also reduces the
+// next CFL signal speed of every cell and carries inactive instances over.
+__global__ void __launch_bounds__(kCellThreads) k_fallback_cells(StageArgs a) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Batch& b = a.b;
+  if (c >= b.ncells) return;
+  const CellPos q = cell_pos(b, c);
+  if (!inst_active(b, q.i)) {
+    // finished or failed instance: carry its start-of-step state into the
+    // step's output buffers (a failed instance stays at its last good state)
+    if (a.stage == 3) {
+      double u[NV], v[NV];
+      load12(a.U0, b.ncells, c, u);
+      load12(a.V0, b.ncells, c, v);
+      store_cell(a, c, u, v);
+    }
+    return;
+  }
+  const InstDesc& I = q.I;
+  bool hit = a.bad[c] != 0;
+  for (int d = 0; d < I.ndim && !hit; ++d) {
+    for (int e = -1; e <= 1; e += 2) {
+      const int pd = q.p[d] + e;
+      if ((pd < 0 || pd >= I.n[d]) && I.bc[d] != 1) continue;  // outflow ghost face
+      int r[3] = {q.p[0], q.p[1], q.p[2]};
+      r[d] = map_idx(pd, I.n[d], I.bc[d]);
+      if (a.bad[I.cell_off + ((int64_t)r[2] * I.n[1] + r[1]) * I.n[0] + r[0]]) hit = true;
+    }
+  }
+  double Vn[NV];
+  if (hit) {
+    double Un[NV];
+    const int rc = cell_update(a, c, q, Un, Vn);
+    if (a.cell_status) a.cell_status[c] = rc;
+    if (rc != ST_OK) {
+      atomicCAS(b.st.status + q.i, 0, rc);
+      return;
+    }
+    store_cell(a, c, Un, Vn);
+  } else if (a.stage == 3) {
+    load12(a.Vout, b.ncells, c, Vn);
+  }
+  if (a.stage == 3) {
+    double s = signal_speed(a.P, 0, Vn) / I.dx[0];
+    for (int d = 1; d < I.ndim; ++d) s = s + signal_speed(a.P, d, Vn) / I.dx[d];
+    atomicMax(b.st.smax + q.i, (unsigned long long)__double_as_longlong(s));
+  }
+}
+
+__global__ void k_signal(Params P, Batch b, const double* __restrict__ V) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= b.ncells) return;
+  const int i = find_inst(b.cell_off, b.n_inst, c);
+  const InstDesc I = b.inst[i];
+  double v[NV];
+  load12(V, b.ncells, c, v);
+  double s = signal_speed(P, 0, v) / I.dx[0];
+  for (int d = 1; d < I.ndim; ++d) s = s + signal_speed(P, d, v) / I.dx[d];
+  atomicMax(b.st.smax + i, (unsigned long long)__double_as_longlong(s));
+}
+
+// dt = CFL / max_cells sum_d lambda_d/dx_d, clipped to land on t_end.
+__global__ void k_begin_step(Params P, Batch b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.n_inst) return;
+  const double t = b.st.t[i], te = b.st.t_end[i];
+  double dt = 0.0;
+  if (b.st.status[i] == 0 && t < te) {
+    const double smax = __longlong_as_double((long long)b.st.smax[i]);
+    dt = P.cfl / smax;
+    if (t + dt > te) dt = te - t;
+    if (!(dt > 0.0)) {  // NaN or non-positive speed bound
+      dt = 0.0;
+      b.st.status[i] = ST_UNPHYS;
+    }
+  }
+  b.st.dt[i] = dt;
+  b.st.smax[i] = 0ull;
+}
+
+__global__ void k_end_step(Batch b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.n_inst) return;
+  if (b.st.status[i] == 0 && b.st.dt[i] > 0.0) b.st.t[i] = b.st.t[i] + b.st.dt[i];
+}
+
+__global__ void k_prim2con(Params P, const double* __restrict__ V, double* __restrict__ U,
+                           int64_t n) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double v[NV], u[NV];
+  load12(V, n, c, v);
+  prim2con(P, v, u);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) U[k * n + c] = u[k];
+}
+
+__global__ void k_prim_Z(Params P, const double* __restrict__ V, double* __restrict__ Z,
+                         int64_t n) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double v[NV];
+  load12(V, n, c, v);
+  Z[c] = prim_Z(P, v);
+}
+
+__global__ void k_con2prim(Params P, const double* __restrict__ U, const double* __restrict__ Zg,
+                           double* __restrict__ V, int32_t* __restrict__ status, int64_t n) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double u[NV], v[NV];
+  load12(U, n, c, u);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  const int rc = con2prim(P, u, Zg ? Zg[c] : 0.0, v, nullptr);
+  if (status) status[c] = rc;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) V[k * n + c] = v[k];
+}
+
+__global__ void k_implicit(Params P, Batch b, double hdt, const double* __restrict__ Us,
+                           const double* __restrict__ Zg, const double* __restrict__ kappa,
+                           const double* __restrict__ sigma, double* __restrict__ U,
+                           double* __restrict__ V, int32_t* __restrict__ status) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = b.ncells;
+  if (c >= n) return;
+  double us[NV], un[NV], vn[NV];
+  load12(Us, n, c, us);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    un[k] = 0.0;
+    vn[k] = 0.0;
+  }
+  const int rc = implicit_cell(P, kappa[c], sigma[c], hdt, us, Zg ? Zg[c] : 0.0, un, vn);
+  if (status) status[c] = rc;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    U[k * n + c] = un[k];
+    V[k * n + c] = vn[k];
+  }
+}
+
+inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+void launch_faces_f64(const StageArgs& a, cudaStream_t s) {
+  const int64_t n = a.f_end - a.f_begin;
+  if (n <= 0) return;
+  k_faces<<<grid_for(n, kFaceThreads), kFaceThreads, 0, s>>>(a);
+}
+
+void launch_cells_f64(const StageArgs& a, cudaStream_t s) {
+  if (a.b.ncells <= 0) return;
+  k_cells<<<grid_for(a.b.ncells, kCellThreads), kCellThreads, 0, s>>>(a);
+}
+
+void launch_fallback_f64(const StageArgs& a, cudaStream_t s) {
+  if (a.b.nfaces > 0)
+    k_fallback_faces<<<grid_for(a.b.nfaces, kFaceThreads), kFaceThreads, 0, s>>>(a);
+  if (a.b.ncells > 0)
+    k_fallback_cells<<<grid_for(a.b.ncells, kCellThreads), kCellThreads, 0, s>>>(a);
+}
+
+void launch_signal_f64(const Params& P, const Batch& b, const double* V, cudaStream_t s) {
+  if (b.ncells <= 0) return;
+  k_signal<<<grid_for(b.ncells, 128), 128, 0, s>>>(P, b, V);
+}
+
+void launch_begin_step(const Params& P, const Batch& b, cudaStream_t s) {
+  k_begin_step<<<grid_for(b.n_inst, 128), 128, 0, s>>>(P, b);
+}
+
+void launch_end_step(const Batch& b, cudaStream_t s) {
+  k_end_step<<<grid_for(b.n_inst, 128), 128, 0, s>>>(b);
+}
+
+void launch_prim2con_f64(const Params& P, const double* V, double* U, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_prim2con<<<grid_for(n, 256), 256, 0, s>>>(P, V, U, n);
+}
+
+void launch_prim_Z_f64(const Params& P, const double* V, double* Z, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_prim_Z<<<grid_for(n, 256), 256, 0, s>>>(P, V, Z, n);
+}
+
+void launch_con2prim_f64(const Params& P, const double* U, const double* Zg, double* V,
+                         int32_t* status, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_con2prim<<<grid_for(n, 128), 128, 0, s>>>(P, U, Zg, V, status, n);
+}
+
+void launch_implicit_f64(const Params& P, const Batch& b, double hdt, const double* Us,
+                         const double* Zg, const double* kappa, const double* sigma, double* U,
+                         double* V, int32_t* status, cudaStream_t s) {
+  if (b.ncells <= 0) return;
+  k_implicit<<<grid_for(b.ncells, kCellThreads), kCellThreads, 0, s>>>(P, b, hdt, Us, Zg, kappa,
+                                                                       sigma, U, V, status);
+}
+
+}  // namespace rr

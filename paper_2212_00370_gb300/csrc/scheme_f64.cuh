@@ -1,0 +1,424 @@
+// scheme_f64.cuh -- FP64 interface and cell operators: PLM reconstruction with
+// the Godunov fallback, the PVM-int-8 Jacobian-free numerical flux, and the
+// implicit radiation-matter solve of one cell (arXiv:2212.00370, Secs. 3.2-3.3).
+// Same arithmetic contract as physics_f64.cuh.
+#pragma once
+#include "physics_f64.cuh"
+
+namespace rr {
+
+// ------------------------------------------------------------ reconstruction
+// Slope limiters of Sec. 3.2 (MinMod, MC, VanLeer); zero slope at extrema.
+__device__ __forceinline__ double limiter(int recon, double dL, double dR) {
+  if (recon == RECON_GODUNOV) return 0.0;
+  if (!(dL * dR > 0.0)) return 0.0;
+  if (recon == RECON_MINMOD) return fabs(dL) < fabs(dR) ? dL : dR;
+  if (recon == RECON_MC) {
+    double m = 2.0 * fabs(dL);
+    const double r = 2.0 * fabs(dR);
+    const double c = fabs(0.5 * (dL + dR));
+    if (r < m) m = r;
+    if (c < m) m = c;
+    return dL > 0.0 ? m : -m;
+  }
+  return ((2.0 * dL) * dR) / (dL + dR);
+}
+
+// Face values of the middle cell: vm at its left face, vp at its right face.
+// Either face with |v|^2 >= 1 or |F_r| > E_r sends the cell to first order.
+__device__ __forceinline__ void reconstruct(int recon, const double* w0, const double* w1,
+                                            const double* w2, double* vm, double* vp) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double s = limiter(recon, w1[k] - w0[k], w2[k] - w1[k]);
+    vp[k] = w1[k] + 0.5 * s;
+    vm[k] = w1[k] - 0.5 * s;
+  }
+  const double v2m = (vm[1] * vm[1] + vm[2] * vm[2]) + vm[3] * vm[3];
+  const double F2m = (vm[9] * vm[9] + vm[10] * vm[10]) + vm[11] * vm[11];
+  const double v2p = (vp[1] * vp[1] + vp[2] * vp[2]) + vp[3] * vp[3];
+  const double F2p = (vp[9] * vp[9] + vp[10] * vp[10]) + vp[11] * vp[11];
+  const bool bad = !(v2m < 1.0) || F2m > vm[8] * vm[8] || !(v2p < 1.0) || F2p > vp[8] * vp[8];
+  if (bad) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      vp[k] = w1[k];
+      vm[k] = w1[k];
+    }
+  }
+}
+
+// ------------------------------------------------------------ PVM-int-8
+// p_3(x) = x^2(x^2(x^2(a0 x^2 + a1) + a2) + a3) + a4 (Eq. iterat with k = 3).
+__device__ __constant__ const double PVM_ALPHA[5] = {-1.0 / 128.0, 3.0 / 32.0, -23.0 / 64.0,
+                                                     31.0 / 32.0, 39.0 / 128.0};
+
+// A(U_m)^2 w by two nested flux differences (Sec. 3.2.2 steps 3-5, Eq. utilde).
+// Returns false if a recovery fails.
+__device__ __forceinline__ bool a2_product(const Params& P, int d, const double* Um,
+                                           const double* Fm, double Zm, const double* w,
+                                           double* out) {
+  double Ue[NV], Ve[NV], Fe[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) Ue[k] = Um[k] + P.pvm_eps * w[k];
+  if (con2prim(P, Ue, Zm, Ve, nullptr) != ST_OK) return false;
+  flux(P, d, Ve, Ue, Fe);
+  // reuse Ue/Ve for U~_eps = U_m + F(U_eps) - F(U_m)
+#pragma unroll
+  for (int k = 0; k < NV; ++k) Ue[k] = Um[k] + (Fe[k] - Fm[k]);
+  if (con2prim(P, Ue, Zm, Ve, nullptr) != ST_OK) return false;
+  flux(P, d, Ve, Ue, Fe);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = (Fe[k] - Fm[k]) / P.pvm_eps;
+  return true;
+}
+
+// F^ = (F_L + F_R)/2 - beta p_3(A(U_m)) (U_R - U_L)/2  (Eqs. generalflux, beta);
+// Q = I (lambda_max = 1 Rusanov) if a recovery inside the viscosity term fails.
+// Returns 1 on that fallback, 0 otherwise.
+__device__ __forceinline__ int pvm_flux(const Params& P, int d, const double* VL,
+                                        const double* VR, double tauL, double tauR,
+                                        double* Fhat) {
+  double Um[NV], U0[NV], Fm[NV], Ul[NV];
+  double ZL, ZR;
+  {
+    double UL[NV], UR[NV], FL[NV], FR[NV];
+    prim2con(P, VL, UL);
+    prim2con(P, VR, UR);
+    flux(P, d, VL, UL, FL);
+    flux(P, d, VR, UR, FR);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      U0[k] = UR[k] - UL[k];
+      Um[k] = 0.5 * (UL[k] + UR[k]);
+      Fhat[k] = 0.5 * (FL[k] + FR[k]);  // central part; viscosity subtracted below
+    }
+    ZL = prim_Z(P, VL);
+    ZR = prim_Z(P, VR);
+  }
+  const double Zg = 0.5 * (ZL + ZR);
+  double beta = 1.0;
+  if (P.beta_mode) {
+    double t = tauL > tauR ? tauL : tauR;
+    if (t < 1.0) t = 1.0;
+    beta = 1.0 / t;
+  }
+  int fail = 0;
+  double Zm = 0.0;
+  {
+    double Vm[NV];
+    if (con2prim(P, Um, Zg, Vm, &Zm) != ST_OK) {
+      fail = 1;
+    } else {
+      flux(P, d, Vm, Um, Fm);
+    }
+  }
+  if (!fail) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) Ul[k] = U0[k];
+    for (int l = 0; l < 4; ++l) {
+      double Y[NV];
+      if (!a2_product(P, d, Um, Fm, Zm, Ul, Y)) {
+        fail = 1;
+        break;
+      }
+      if (l == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) Ul[k] = PVM_ALPHA[0] * Y[k] + PVM_ALPHA[1] * U0[k];
+      } else {
+        const double al = PVM_ALPHA[l + 1];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) Ul[k] = Y[k] + al * U0[k];
+      }
+    }
+  }
+  if (fail) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) Ul[k] = U0[k];
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) Fhat[k] = Fhat[k] - 0.5 * (beta * Ul[k]);
+  return fail;
+}
+
+// First-order Rusanov flux with lambda_max = 1 (Q = I in Eq. generalflux) from
+// the cell-centre states; used only by the admissibility fallback.
+__device__ __forceinline__ void llf_flux(const Params& P, int d, const double* VL,
+                                         const double* VR, double* Fhat) {
+  double UL[NV], UR[NV], FL[NV], FR[NV];
+  prim2con(P, VL, UL);
+  prim2con(P, VR, UR);
+  flux(P, d, VL, UL, FL);
+  flux(P, d, VR, UR, FR);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) Fhat[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * (UR[k] - UL[k]);
+}
+
+// ------------------------------------------------------------ implicit step
+// Per cell, solve R(X) = X - X* + h G(X, V(X)) = 0 for X = (E_r, F_r), with the
+// magnetofluid from the conserved totals tau_t = tau* + E*, S_t = S* + F*
+// (Eqs. timeadv, totale, totalm) and V(X) its con2prim (Sec. 3.3 step 5).
+struct ImpCell {
+  double kappa, sigma, hdt;
+  double D, St[3], taut, B[3], Xs[4];
+};
+
+__device__ __forceinline__ void matter_state(const ImpCell& c, const double* X, double* Um) {
+  Um[0] = c.D;
+  Um[1] = c.St[0] - X[1];
+  Um[2] = c.St[1] - X[2];
+  Um[3] = c.St[2] - X[3];
+  Um[4] = c.taut - X[0];
+  Um[5] = c.B[0];
+  Um[6] = c.B[1];
+  Um[7] = c.B[2];
+  Um[8] = X[0];
+  Um[9] = X[1];
+  Um[10] = X[2];
+  Um[11] = X[3];
+}
+
+// Returns false if X is inadmissible (E_r <= 0 or no con2prim root).
+static __device__ __noinline__ bool imp_residual(const Params& P, const ImpCell& c, const double* X,
+                                          double Zg, double* R, double* V, double* Z) {
+  if (!(X[0] > 0.0)) return false;
+  double Um[NV];
+  matter_state(c, X, Um);
+  if (con2prim(P, Um, Zg, V, Z) != ST_OK) return false;
+  const double v2 = (V[1] * V[1] + V[2] * V[2]) + V[3] * V[3];
+  const double W = 1.0 / sqrt(1.0 - v2);
+  const double u[3] = {W * V[1], W * V[2], W * V[3]};
+  const double T = V[4] / V[0];
+  const double BP = P.a_rad * ((T * T) * (T * T));
+  const M1 m = m1_coef(X[0], X[1], X[2], X[3]);
+  double Pr[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Pr[i][j] = m1_P(m, X + 1, i, j);
+  double G[4];
+  four_force(c.kappa, c.sigma, V[0], u, W, BP, X[0], X + 1, Pr, G);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) R[i] = (X[i] - c.Xs[i]) + c.hdt * G[i];
+  return true;
+}
+
+// Gaussian elimination with partial pivoting (A, b overwritten); false if singular.
+__device__ __forceinline__ bool solve4(double A[4][4], double b[4], double x[4]) {
+#pragma unroll
+  for (int col = 0; col < 4; ++col) {
+    int piv = col;
+#pragma unroll
+    for (int r = col + 1; r < 4; ++r)
+      if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+    if (A[piv][col] == 0.0) return false;
+    if (piv != col) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double t = A[col][k];
+        A[col][k] = A[piv][k];
+        A[piv][k] = t;
+      }
+      const double t = b[col];
+      b[col] = b[piv];
+      b[piv] = t;
+    }
+#pragma unroll
+    for (int r = col + 1; r < 4; ++r) {
+      const double f = A[r][col] / A[col][col];
+#pragma unroll
+      for (int k = col + 1; k < 4; ++k) A[r][k] = A[r][k] - f * A[col][k];
+      b[r] = b[r] - f * b[col];
+    }
+  }
+#pragma unroll
+  for (int r = 3; r >= 0; --r) {
+    double s = b[r];
+#pragma unroll
+    for (int k = r + 1; k < 4; ++k) s = s - A[r][k] * x[k];
+    x[r] = s / A[r][r];
+  }
+  return true;
+}
+
+// C^(m) of Sec. 3.3 step 2 (matter and Eddington tensor frozen), with the
+// C_{i+1,j+1} sign derived from Eqs. g0/gi: delta + h rho W[(k+s) delta + 2 s u u].
+__device__ __forceinline__ void picard_matrix(const ImpCell& c, const double* X,
+                                              const double* V, double J[4][4]) {
+  const double v2 = (V[1] * V[1] + V[2] * V[2]) + V[3] * V[3];
+  const double W = 1.0 / sqrt(1.0 - v2);
+  const double u[3] = {W * V[1], W * V[2], W * V[3]};
+  const double rho = V[0];
+  double Dr[3][3];
+  eddington(X[0], X + 1, Dr);
+  const double u2 = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
+  double Du[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Du[i] = (Dr[i][0] * u[0] + Dr[i][1] * u[1]) + Dr[i][2] * u[2];
+  const double uDu = (u[0] * Du[0] + u[1] * Du[1]) + u[2] * Du[2];
+  const double ks = c.kappa + c.sigma;
+  const double h = c.hdt;
+  J[0][0] = 1.0 - h * ((rho * W) * (-c.kappa + c.sigma * (u2 + uDu)));
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    J[0][1 + j] = -h * ((rho * u[j]) * (c.kappa - c.sigma * (2.0 * u2 + 1.0)));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    J[1 + i][0] = -h * (rho * (ks * Du[i] + (c.sigma * u[i]) * ((W * W) + uDu)));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double t = h * ((rho * W) * ((i == j ? ks : 0.0) + (2.0 * c.sigma) * (u[i] * u[j])));
+      J[1 + i][1 + j] = (i == j ? 1.0 : 0.0) + t;
+    }
+  }
+}
+
+// Newton iteration starting from the C^(m) matrix; full forward-difference
+// Jacobian (step 1e-7 E_r) once successive steps contract by less than 4x or a
+// step gives no descent; Armijo backtracking on |R|^2; converged when the full
+// step is <= imp_tol * E_r.  Returns true on convergence.
+static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c, double* X, double* R,
+                                        double* V, double* Z) {
+  double J[4][4];
+  int full = 0, jac_age = 0, need_full = 0;
+  double prev = -1.0;
+  for (int m = 1; m <= P.imp_maxit; ++m) {
+    if (need_full) {
+      const double h = 1e-7 * X[0];
+      for (int j = 0; j < 4; ++j) {
+        double Xp[4] = {X[0], X[1], X[2], X[3]};
+        double Rp[4], Vp[NV], Zp;
+        Xp[j] = X[j] + h;
+        if (!imp_residual(P, c, Xp, *Z, Rp, Vp, &Zp)) {
+          Xp[j] = X[j] - h;
+          if (!imp_residual(P, c, Xp, *Z, Rp, Vp, &Zp)) return false;
+        }
+        const double dXj = Xp[j] - X[j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) J[i][j] = (Rp[i] - R[i]) / dXj;
+      }
+      full = 1;
+      need_full = 0;
+      jac_age = 0;
+    } else if (!full) {
+      picard_matrix(c, X, V, J);
+    }
+    double A[4][4], b[4], dX[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      b[i] = -R[i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) A[i][j] = J[i][j];
+    }
+    if (!solve4(A, b, dX)) return false;
+
+    double dfull = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dfull = fabs(dX[i]) > dfull ? fabs(dX[i]) : dfull;
+    double Xn[4], Rn[4], Vn[NV], Zn = *Z;
+    if (dfull <= P.imp_tol * X[0]) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Xn[i] = X[i] + dX[i];
+      if (!imp_residual(P, c, Xn, *Z, Rn, Vn, &Zn)) return false;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        X[i] = Xn[i];
+        R[i] = Rn[i];
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) V[k] = Vn[k];
+      *Z = Zn;
+      return true;
+    }
+    const double r0 = ((R[0] * R[0] + R[1] * R[1]) + R[2] * R[2]) + R[3] * R[3];
+    double lam = 1.0;
+    int ok = 0;
+    for (int k = 0; k < 40; ++k) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Xn[i] = X[i] + dX[i];
+      if (imp_residual(P, c, Xn, *Z, Rn, Vn, &Zn)) {
+        const double r1 = ((Rn[0] * Rn[0] + Rn[1] * Rn[1]) + Rn[2] * Rn[2]) + Rn[3] * Rn[3];
+        if (r1 <= (1.0 - 1e-4 * lam) * r0) {
+          ok = 1;
+          break;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) dX[i] = 0.5 * dX[i];
+      lam = 0.5 * lam;
+      if (!full && k == 3) break;
+    }
+    if (!ok) {
+      if (!full || jac_age > 0) {
+        need_full = 1;
+        continue;
+      }
+      return false;
+    }
+    jac_age++;
+    double dmax = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double dd = fabs(dX[i]);
+      if (dd > dmax) dmax = dd;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      X[i] = Xn[i];
+      R[i] = Rn[i];
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) V[k] = Vn[k];
+    *Z = Zn;
+    if (prev >= 0.0 && dmax > 0.25 * prev) need_full = 1;
+    prev = dmax;
+  }
+  return false;
+}
+
+constexpr int IMP_LADDER = 6;  // continuation fallback starts at h / 2^6
+
+// Implicit step of one cell (Sec. 3.3).  Writes U and V on success; returns a Status.
+__device__ __forceinline__ int implicit_cell(const Params& P, double kappa, double sigma,
+                                             double hdt, const double* Us, double Zguess,
+                                             double* U, double* V) {
+  if ((kappa == 0.0 && sigma == 0.0) || hdt == 0.0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) U[k] = Us[k];
+    return con2prim(P, Us, Zguess, V, nullptr);
+  }
+  ImpCell c;
+  c.kappa = kappa;
+  c.sigma = sigma;
+  c.hdt = hdt;
+  c.D = Us[0];
+  c.taut = Us[4] + Us[8];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    c.St[j] = Us[1 + j] + Us[9 + j];
+    c.B[j] = Us[5 + j];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) c.Xs[i] = Us[8 + i];
+  double X[4] = {c.Xs[0], c.Xs[1], c.Xs[2], c.Xs[3]};
+  double R[4], Z = Zguess;
+  // no admissible matter state at X*: the explicit update U* itself is inadmissible
+  if (!imp_residual(P, c, X, Zguess, R, V, &Z)) return ST_C2P;
+  bool ok = imp_newton(P, c, X, R, V, &Z);
+  if (!ok) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) X[i] = c.Xs[i];
+    Z = Zguess;
+    ok = true;
+    for (int j = IMP_LADDER; j >= 0 && ok; --j) {
+      c.hdt = hdt / (double)(1 << j);
+      ok = imp_residual(P, c, X, Z, R, V, &Z);
+      if (ok) ok = imp_newton(P, c, X, R, V, &Z);
+    }
+  }
+  if (!ok) return ST_IMPLICIT;
+  matter_state(c, X, U);
+  return ST_OK;
+}
+
+}  // namespace rr
