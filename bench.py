@@ -33,10 +33,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # FP64-pipe instructions (DADD + DMUL + DFMA, thread level, ncu
-# smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum) per zone-update
-# of each launch group on this workload; measured once with ncu on a 512-instance
-# sample of the same distribution (profiles/c1_fp64_kernels.md).  0 = not yet measured.
-FP64_INST_PER_ZONE = {"faces": 0.0, "cells": 0.0}
+# sm__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum) per cell of ONE launch
+# of each kernel on this workload, measured with ncu on a 2048-instance sample of the
+# same distribution (profiles/c1_fp64_k_cells_k_faces.md).  0 = not measured for the
+# current kernel.
+FP64_INST_PER_ZONE = {"faces": 5712.0, "cells": 0.0}
 # Nominal FP64 rate of GB300: 1.25 TFLOP/s = 6.25e11 FP64-pipe instructions/s
 # (2 per SM per clock on 152 SMs at 2.07 GHz); no MEASURED_PEAKS entry exists for FP64.
 FP64_PEAK_INST = 6.25e11
@@ -53,6 +54,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=256, help="instances in the CPU sample")
+    p.add_argument("--lanes", type=int, default=8, help="independent sub-batches (streams)")
     return p.parse_args()
 
 
@@ -164,7 +166,7 @@ def run_ours(a, rank, world, pool, cores):
     seed = W.SEED_BASE + 1 + rank
     w = W.riemann_batch(a.instances, seed=seed)
     grids = [rrmhd.make_grid(1, g["n"], g["dx"], g["bc"]) for g in w.grids]
-    ctx = rrmhd.Context(grids, gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl)
+    ctx = rrmhd.Context(grids, gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl, lanes=a.lanes)
     ctx.set_opacity(torch.tensor(w.kappa, device="cuda"), torch.tensor(w.sigma, device="cuda"))
     V0 = torch.tensor(w.V, device="cuda")
     ctx.set_state(V0)
@@ -213,18 +215,20 @@ def run_ours(a, rank, world, pool, cores):
         prof += ctx.profile_step()
     prof /= nprof
     zones_step = float(n_cells[live].sum())
-    groups = {"faces": prof[0] / 3.0, "cells": prof[1] / 3.0}   # ms per launch
+    groups = {"faces": prof[0] / 3.0, "cells": prof[1] / 3.0}   # ms per (whole-batch) launch
     dom = max(groups, key=groups.get)
     per_zone = FP64_INST_PER_ZONE[dom]
-    # per launch: (instructions per zone-update of this group) x zone-updates / 3 launches
-    achieved = per_zone * zones_step / 3.0 / (groups[dom] / 1e3) if per_zone else None
+    # algorithmic FP64 instructions of one launch / its duration
+    achieved = per_zone * zones_step / (groups[dom] / 1e3) if per_zone else None
     roofline = {
         "bound": "alu", "kernel": "k_" + dom + " (FP64)",
         "achieved": achieved, "peak": FP64_PEAK_INST, "unit": "FP64-pipe inst/s",
         "frac": (achieved / FP64_PEAK_INST) if achieved else None,
         "traffic": None,
         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe; no measured FP64 peak)",
-        "launch_ms": {k: round(v, 4) for k, v in groups.items()},
+        "launch_ms": {"faces": round(groups["faces"], 4), "cells": round(groups["cells"], 4),
+                      "fallback": round(prof[2] / 3.0, 4), "step_control": round(prof[3] / 2.0, 4)},
+        "faces_fp64_frac": (FP64_INST_PER_ZONE["faces"] * zones_step / (groups["faces"] / 1e3)) / FP64_PEAK_INST,
         "hbm_frac": BYTES_PER_ZONE_STEP * value / (6791.7e9),
     }
 
@@ -259,7 +263,7 @@ def run_ours(a, rank, world, pool, cores):
                                % a.instances,
                    "instances": a.instances, "cells": int(n_cells.sum()),
                    "live_instances": int(live.sum()), "failed_instances": int((~live).sum()),
-                   "parallelism": "replicas (independent problems per GPU)",
+                   "parallelism": "replicas (independent problems per GPU); %d lanes (streams) per GPU" % a.lanes,
                    "l2": "state %.0f MB per copy > 129 MB L2 (inputs larger than L2)" % (12 * 8 * w.ncells / 1e6)},
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
         "roofline": roofline,

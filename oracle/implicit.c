@@ -179,20 +179,27 @@ static void picard_jacobian(const imp_ctx* c, const double X[4], const double V[
     or_picard_matrix(c->kappa, c->sigma, c->hdt, V[0], u, W, 0.0, Dr, c->Xs, J, rhs);
 }
 
-/* Newton iteration on R(X) = 0.  The first matrix is the paper's C^(m) (the
- * exact Jacobian with matter and Eddington tensor frozen), so the first
- * iterates are the iteration of Sec. 3.3; when they contract slowly (ratio of
- * successive steps > 1/4) or give no descent, the full Jacobian is formed by
- * forward differences (step 1e-7 E_r) and kept while it contracts well.
- * Every step is damped by a backtracking line search on |R|^2. */
+/* Quasi-Newton iteration on R(X) = 0.
+ * The first matrix is the paper's C^(m) (the Jacobian with matter and Eddington
+ * tensor frozen), so the first iterate is the iteration of Sec. 3.3.  Each
+ * accepted step then updates the matrix by Broyden's rank-one formula
+ * J += (dR - J dX) dX^T / (dX.dX), which learns the matter coupling (T^4,
+ * recoil) the frozen matrix leaves out.  When successive steps contract by less
+ * than 2x, or a step gives no descent, the matrix is replaced by a
+ * forward-difference Jacobian (step 1e-7 E_r).  Every step is damped by a
+ * backtracking line search on |R|^2 (Armijo 1e-4); converged when the full step
+ * is <= imp_tol * E_r. */
 static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z)
 {
     const or_params* P = c->P;
     double J[4][4];
-    int full = 0, jac_age = 0, need_full = 0;
+    int need_fd = 0;      /* replace J by a forward-difference Jacobian          */
+    int fresh_fd = 0;     /* J is an FD Jacobian at the current X, not updated   */
+    int first = 1;        /* J is the initial frozen-matter matrix C^(m)         */
     double prev = -1.0;
+    picard_jacobian(c, X, V, J);
     for (int m = 1; m <= P->imp_maxit; m++) {
-        if (need_full) {
+        if (need_fd) {
             double h = 1e-7 * X[0];
             for (int j = 0; j < 4; j++) {
                 double Xp[4] = {X[0], X[1], X[2], X[3]};
@@ -205,19 +212,20 @@ static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z)
                 double dXj = Xp[j] - X[j];
                 for (int i = 0; i < 4; i++) J[i][j] = (Rp[i] - R[i]) / dXj;
             }
-            full = 1;
-            need_full = 0;
-            jac_age = 0;
+            need_fd = 0;
+            fresh_fd = 1;
+            first = 0;
             if (c->st) c->st->imp_jac++;
-        } else if (!full) {
-            picard_jacobian(c, X, V, J);
         }
         double A[4][4], b[4], dX[4];
         for (int i = 0; i < 4; i++) {
             b[i] = -R[i];
             for (int j = 0; j < 4; j++) A[i][j] = J[i][j];
         }
-        if (or_solve4(A, b, dX)) return 1;
+        if (or_solve4(A, b, dX)) {
+            if (!fresh_fd) { need_fd = 1; continue; }
+            return 1;
+        }
         if (c->st) c->st->imp_iters++;
 
         /* converged when the full step is below tolerance: take it and stop */
@@ -235,8 +243,9 @@ static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z)
             *Z = Zn;
             return 0;
         }
-        /* damped update (backtracking line search): halve the step until the
-         * matter state is admissible and |R|^2 decreases (Armijo, 1e-4) */
+        /* backtracking line search: halve the step until the matter state is
+         * admissible and |R|^2 decreases (the initial frozen-matter matrix gets
+         * four halvings before the full Jacobian replaces it) */
         double r0 = ((R[0] * R[0] + R[1] * R[1]) + R[2] * R[2]) + R[3] * R[3];
         double lam = 1.0;
         int ok = 0;
@@ -248,18 +257,29 @@ static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z)
             }
             for (int i = 0; i < 4; i++) dX[i] = 0.5 * dX[i];
             lam = 0.5 * lam;
-            if (!full && k == 3) break;   /* the frozen-matter matrix gives no descent */
+            if (first && k == 3) break;
         }
         if (!ok) {
-            /* no acceptable step: form the full Jacobian here and retry */
-            if (!full || jac_age > 0) { need_full = 1; continue; }
+            if (!fresh_fd) { need_fd = 1; continue; }
             return 1;
         }
-        jac_age++;
         double dmax = 0.0;
         for (int i = 0; i < 4; i++) {
             double d = fabs(dX[i]);
             if (d > dmax) dmax = d;
+        }
+        /* Broyden update with the accepted step dX and residual change */
+        {
+            double dR[4];
+            for (int i = 0; i < 4; i++) dR[i] = Rn[i] - R[i];
+            double s2 = ((dX[0] * dX[0] + dX[1] * dX[1]) + dX[2] * dX[2]) + dX[3] * dX[3];
+            for (int i = 0; i < 4; i++) {
+                double Jd = ((J[i][0] * dX[0] + J[i][1] * dX[1]) + J[i][2] * dX[2]) + J[i][3] * dX[3];
+                double q = (dR[i] - Jd) / s2;
+                for (int j = 0; j < 4; j++) J[i][j] = J[i][j] + q * dX[j];
+            }
+            fresh_fd = 0;
+            first = 0;
         }
         for (int i = 0; i < 4; i++) {
             X[i] = Xn[i];
@@ -267,8 +287,8 @@ static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z)
         }
         for (int k = 0; k < 12; k++) V[k] = Vn[k];
         *Z = Zn;
-        /* slow contraction: switch to (or refresh) the full Jacobian at the new point */
-        if (prev >= 0.0 && dmax > 0.25 * prev) need_full = 1;
+        /* slow contraction: replace J by the full Jacobian at the new point */
+        if (prev >= 0.0 && dmax > 0.5 * prev) need_fd = 1;
         prev = dmax;
     }
     return 1;

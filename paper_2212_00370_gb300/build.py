@@ -42,7 +42,8 @@ def _stale():
 
 def _compile(unit, flags, verbose):
     obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
-    cmd = [NVCC, *ARCH, *COMMON, *flags, "-c", os.path.join(CSRC, unit), "-o", obj]
+    extra = os.environ.get("RRMHD_NVCC_FLAGS", "").split()   # tuning knobs, e.g. -DRR_CELL_MIN_BLOCKS=2
+    cmd = [NVCC, *ARCH, *COMMON, *flags, *extra, "-c", os.path.join(CSRC, unit), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -42,6 +42,11 @@ struct Batch {
   const int64_t* cell_off;   // [n_inst + 1]
   const int64_t* face_off;   // [3][n_inst + 1] (prefix sums within each direction)
   InstState st;
+  // the part of the batch a launch covers (a lane: contiguous instances)
+  int i_begin, i_end;        // instances
+  int64_t c_begin, c_end;    // cells
+  int64_t f_begin[3];        // faces of direction d: [f_begin[d], f_begin[d] + f_count[d])
+  int64_t f_count[3];
 };
 
 struct StageArgs {
@@ -56,7 +61,6 @@ struct StageArgs {
   const double* sigma;
   double* Fhat;            // [12][fstride]; face g is stored at column g - out_base
   int64_t fstride;
-  int64_t f_begin, f_end;  // face range handled by a face launch
   int64_t out_base;
   int check_active;        // skip instances that are finished or failed
   double* Uout;            // must not alias U0, Us, Vs (the fallback pass re-reads them)

@@ -18,6 +18,13 @@ using rr::InstDesc;
 using rr::Params;
 using rr::StageArgs;
 
+struct Lane {
+  Batch b;                      // the lane's instance / cell / face ranges
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per value of rrmhd_ctx::cur
+};
+
 struct rrmhd_ctx {
   rrmhd_opts opts;
   Params P;
@@ -41,7 +48,8 @@ struct rrmhd_ctx {
   double *t = nullptr, *t_end = nullptr, *dt = nullptr;
   unsigned long long* smax = nullptr;
   int* status = nullptr;
-  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};  // one per value of cur
+  std::vector<Lane> lanes;
+  cudaEvent_t fork = nullptr;
   std::string err;
 };
 
@@ -97,14 +105,38 @@ Batch batch_of(const rrmhd_ctx* c) {
   b.st.dt = c->dt;
   b.st.smax = c->smax;
   b.st.status = c->status;
+  b.i_begin = 0;
+  b.i_end = c->n_inst;
+  b.c_begin = 0;
+  b.c_end = c->ncells;
+  for (int d = 0; d < 3; ++d) {
+    b.f_begin[d] = c->dir_base[d];
+    b.f_count[d] = c->dir_base[d + 1] - c->dir_base[d];
+  }
   return b;
 }
 
-StageArgs stage_args(const rrmhd_ctx* c, int stage, const double* U0, const double* V0,
-                     const double* Us, const double* Vs, double* Uout, double* Vout) {
+// Batch restricted to instances [i0, i1).
+Batch sub_batch(const rrmhd_ctx* c, int i0, int i1) {
+  Batch b = batch_of(c);
+  b.i_begin = i0;
+  b.i_end = i1;
+  b.c_begin = c->cell_off[i0];
+  b.c_end = c->cell_off[i1];
+  for (int d = 0; d < 3; ++d) {
+    const int64_t* fo = &c->face_off[(size_t)d * (c->n_inst + 1)];
+    b.f_begin[d] = c->dir_base[d] + fo[i0];
+    b.f_count[d] = fo[i1] - fo[i0];
+  }
+  return b;
+}
+
+StageArgs stage_args(const rrmhd_ctx* c, const Batch& b, int stage, const double* U0,
+                     const double* V0, const double* Us, const double* Vs, double* Uout,
+                     double* Vout) {
   StageArgs a;
   a.P = c->P;
-  a.b = batch_of(c);
+  a.b = b;
   a.stage = stage;
   a.U0 = U0;
   a.V0 = V0;
@@ -114,8 +146,6 @@ StageArgs stage_args(const rrmhd_ctx* c, int stage, const double* U0, const doub
   a.sigma = c->sigma;
   a.Fhat = c->Fhat;
   a.fstride = c->nfaces;
-  a.f_begin = 0;
-  a.f_end = c->nfaces;
   a.out_base = 0;
   a.check_active = 1;
   a.Uout = Uout;
@@ -125,21 +155,20 @@ StageArgs stage_args(const rrmhd_ctx* c, int stage, const double* U0, const doub
   return a;
 }
 
-// One IMEX-RK3 step from the state in buffer set A = S[cur] into B = S[1-cur],
-// with C = (Ub,Vb) for stage 2:  stage 1 A -> B, stage 2 (B; A) -> C,
-// stage 3 (C; A) -> B.  No stage writes its inputs, so the admissibility
-// fallback can re-read them.  Launches: begin, 3 x {faces, cells, fallback
-// faces, fallback cells}, end.
-void enqueue_step(const rrmhd_ctx* c, int cur, cudaStream_t s) {
-  const Batch b = batch_of(c);
+// One IMEX-RK3 step of the instances of b, from the state in buffer set
+// A = S[cur] into B = S[1-cur], with C = (Ub,Vb) for stage 2:
+// stage 1 A -> B, stage 2 (B; A) -> C, stage 3 (C; A) -> B.  No stage writes its
+// inputs, so the admissibility fallback can re-read them.  Launches: begin,
+// 3 x {faces, cells, fallback faces, fallback cells}, end.
+void enqueue_step(const rrmhd_ctx* c, const Batch& b, int cur, cudaStream_t s) {
   double* AU = cur ? c->Ua : c->U0;
   double* AV = cur ? c->Va : c->V0;
   double* BU = cur ? c->U0 : c->Ua;
   double* BV = cur ? c->V0 : c->Va;
   rr::launch_begin_step(c->P, b, s);
-  const StageArgs s1 = stage_args(c, 1, AU, AV, AU, AV, BU, BV);
-  const StageArgs s2 = stage_args(c, 2, AU, AV, BU, BV, c->Ub, c->Vb);
-  const StageArgs s3 = stage_args(c, 3, AU, AV, c->Ub, c->Vb, BU, BV);
+  const StageArgs s1 = stage_args(c, b, 1, AU, AV, AU, AV, BU, BV);
+  const StageArgs s2 = stage_args(c, b, 2, AU, AV, BU, BV, c->Ub, c->Vb);
+  const StageArgs s3 = stage_args(c, b, 3, AU, AV, c->Ub, c->Vb, BU, BV);
   for (const StageArgs* a : {&s1, &s2, &s3}) {
     rr::launch_faces_f64(*a, s);
     rr::launch_cells_f64(*a, s);
@@ -201,14 +230,21 @@ void rrmhd_default_opts(rrmhd_opts* o) {
   o->c2p_maxit = 60;
   o->imp_maxit = 50;
   o->imp_tol = 1e-12;
+  o->lanes = 8;
 }
 
 void rrmhd_destroy(rrmhd_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  for (cudaGraphExec_t g : c->step_graph)
-    if (g) cudaGraphExecDestroy(g);
+  for (Lane& L : c->lanes) {
+    if (L.stream) cudaStreamSynchronize(L.stream);
+    for (cudaGraphExec_t g : L.graph)
+      if (g) cudaGraphExecDestroy(g);
+    if (L.done) cudaEventDestroy(L.done);
+    if (L.stream) cudaStreamDestroy(L.stream);
+  }
+  if (c->fork) cudaEventDestroy(c->fork);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->d_inst, c->d_cell_off, c->d_face_off, c->U0, c->Ua, c->Ub, c->V0,
                   c->Va,     c->Vb,         c->kappa,      c->sigma, c->Fhat, c->t, c->t_end,
@@ -226,7 +262,7 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
   const rrmhd_opts& o = *opts;
   if (!(o.gamma > 1.0) || !(o.a_rad >= 0.0) || !(o.cfl > 0.0) || !(o.pvm_eps > 0.0) ||
       o.recon < 0 || o.recon > 3 || o.c2p_maxit < 1 || o.imp_maxit < 1 || !(o.imp_tol > 0.0) ||
-      (o.precision != RRMHD_FP64 && o.precision != RRMHD_FP32_BULK))
+      (o.precision != RRMHD_FP64 && o.precision != RRMHD_FP32_BULK) || o.lanes < 1)
     return RRMHD_EINVAL;
   if (o.precision != RRMHD_FP64) return RRMHD_EINVAL;  // FP32-bulk kernels: see rrmhd_f32.cu
   std::string why;
@@ -312,6 +348,26 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
     A(cuda_check(c, cudaMemsetAsync(c->V0, 0, sizeof(double) * N12, st), "memset"));
     A(cuda_check(c, cudaMemsetAsync(c->bad, 0, (size_t)c->ncells, st), "memset"));
     A(cuda_check(c, cudaStreamSynchronize(st), "sync"));  // host vectors go out of scope
+  }
+  if (s == RRMHD_OK) {
+    // lanes: contiguous instance ranges of about equal cell count
+    const int L = std::min(o.lanes, n_inst);
+    int i0 = 0;
+    for (int l = 0; l < L && s == RRMHD_OK; ++l) {
+      int i1 = n_inst;
+      if (l < L - 1) {
+        const int64_t target = (c->ncells * (l + 1)) / L;
+        i1 = i0 + 1;
+        while (i1 < n_inst - (L - 1 - l) && c->cell_off[i1] < target) ++i1;
+      }
+      Lane lane;
+      lane.b = sub_batch(c, i0, i1);
+      A(cuda_check(c, cudaStreamCreateWithFlags(&lane.stream, cudaStreamNonBlocking), "stream"));
+      A(cuda_check(c, cudaEventCreateWithFlags(&lane.done, cudaEventDisableTiming), "event"));
+      c->lanes.push_back(lane);
+      i0 = i1;
+    }
+    A(cuda_check(c, cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming), "event"));
   }
   if (s != RRMHD_OK) {
     rrmhd_destroy(c);
@@ -408,29 +464,37 @@ rrmhd_status rrmhd_get_inst_status(const rrmhd_ctx* c, int32_t* status) {
   return RRMHD_OK;
 }
 
-static rrmhd_status build_step_graph(rrmhd_ctx* c, int cur) {
-  if (c->step_graph[cur]) return RRMHD_OK;
+static rrmhd_status build_step_graph(rrmhd_ctx* c, Lane& L, int cur) {
+  if (L.graph[cur]) return RRMHD_OK;
   if (!c->cap_stream)
     RR_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   RR_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  enqueue_step(c, cur, c->cap_stream);
+  enqueue_step(c, L.b, cur, c->cap_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
   if (e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     return cuda_check(c, e, "cudaStreamEndCapture");
   }
-  e = cudaGraphInstantiate(&c->step_graph[cur], g, 0);
+  e = cudaGraphInstantiate(&L.graph[cur], g, 0);
   cudaGraphDestroy(g);
   return cuda_check(c, e, "cudaGraphInstantiate");
 }
 
+// Each step: the lanes fork from the caller's stream, run their step graph
+// concurrently on their own streams, and join back into it.
 rrmhd_status rrmhd_imex_step(rrmhd_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return set_err(c, RRMHD_EINVAL, "bad argument");
   for (int k = 0; k < nsteps; ++k) {
-    rrmhd_status s = build_step_graph(c, c->cur);
-    if (s != RRMHD_OK) return s;
-    RR_CUDA(c, cudaGraphLaunch(c->step_graph[c->cur], c->stream));
+    RR_CUDA(c, cudaEventRecord(c->fork, c->stream));
+    for (Lane& L : c->lanes) {
+      rrmhd_status s = build_step_graph(c, L, c->cur);
+      if (s != RRMHD_OK) return s;
+      RR_CUDA(c, cudaStreamWaitEvent(L.stream, c->fork, 0));
+      RR_CUDA(c, cudaGraphLaunch(L.graph[c->cur], L.stream));
+      RR_CUDA(c, cudaEventRecord(L.done, L.stream));
+    }
+    for (Lane& L : c->lanes) RR_CUDA(c, cudaStreamWaitEvent(c->stream, L.done, 0));
     c->cur ^= 1;
   }
   return RRMHD_OK;
@@ -473,11 +537,11 @@ rrmhd_status rrmhd_con2prim(rrmhd_ctx* c, const double* U, const double* Zguess,
 
 rrmhd_status rrmhd_flux_sweep(rrmhd_ctx* c, int dir, double* Fhat) {
   if (!c || !Fhat || dir < 0 || dir > 2) return set_err(c, RRMHD_EINVAL, "bad argument");
-  StageArgs a = stage_args(c, 0, cur_U(c), cur_V(c), cur_U(c), cur_V(c), nullptr, nullptr);
+  Batch b = batch_of(c);
+  for (int d = 0; d < 3; ++d) b.f_count[d] = (d == dir) ? b.f_count[d] : 0;
+  StageArgs a = stage_args(c, b, 0, cur_U(c), cur_V(c), cur_U(c), cur_V(c), nullptr, nullptr);
   a.Fhat = Fhat;
   a.fstride = c->dir_base[dir + 1] - c->dir_base[dir];
-  a.f_begin = c->dir_base[dir];
-  a.f_end = c->dir_base[dir + 1];
   a.out_base = c->dir_base[dir];
   a.check_active = 0;
   rr::launch_faces_f64(a, c->stream);
@@ -494,7 +558,9 @@ rrmhd_status rrmhd_implicit_source(rrmhd_ctx* c, double hdt, const double* Ustar
   return RRMHD_OK;
 }
 
-int rrmhd_launches_per_step(const rrmhd_ctx* c) { return c ? 2 + 3 * 4 : 0; }
+int rrmhd_launches_per_step(const rrmhd_ctx* c) {
+  return c ? (int)c->lanes.size() * (2 + 3 * 4) : 0;
+}
 
 rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
   if (!c || !ms) return set_err(c, RRMHD_EINVAL, "bad argument");
@@ -504,9 +570,9 @@ rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
   double* AV = cur ? c->Va : c->V0;
   double* BU = cur ? c->U0 : c->Ua;
   double* BV = cur ? c->V0 : c->Va;
-  const StageArgs st[3] = {stage_args(c, 1, AU, AV, AU, AV, BU, BV),
-                           stage_args(c, 2, AU, AV, BU, BV, c->Ub, c->Vb),
-                           stage_args(c, 3, AU, AV, c->Ub, c->Vb, BU, BV)};
+  const StageArgs st[3] = {stage_args(c, b, 1, AU, AV, AU, AV, BU, BV),
+                           stage_args(c, b, 2, AU, AV, BU, BV, c->Ub, c->Vb),
+                           stage_args(c, b, 3, AU, AV, c->Ub, c->Vb, BU, BV)};
   cudaEvent_t ev[14];
   for (auto& e : ev) RR_CUDA(c, cudaEventCreate(&e));
   cudaStream_t s = c->stream;

@@ -24,10 +24,17 @@ namespace {
 
 constexpr int kFaceThreads = 128;
 constexpr int kCellThreads = 128;
+// Resident blocks per SM requested from the register allocator (launch-bounds
+// tuning knobs; 255 registers per thread at 1).
+#ifndef RR_FACE_MIN_BLOCKS
+#define RR_FACE_MIN_BLOCKS 1
+#endif
+#ifndef RR_CELL_MIN_BLOCKS
+#define RR_CELL_MIN_BLOCKS 1
+#endif
 
-// largest i in [0, n) with off[i] <= g  (off non-decreasing, off[0] = 0)
-__device__ __forceinline__ int find_inst(const int64_t* off, int n, int64_t g) {
-  int lo = 0, hi = n;
+// largest i in [lo, hi) with off[i] <= g  (off non-decreasing, off[lo] <= g)
+__device__ __forceinline__ int find_inst(const int64_t* off, int lo, int hi, int64_t g) {
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
     if (off[mid] <= g)
@@ -56,24 +63,50 @@ __device__ __forceinline__ bool inst_active(const Batch& b, int i) {
   return b.st.status[i] == 0 && b.st.dt[i] > 0.0;
 }
 
-__global__ void __launch_bounds__(kFaceThreads) k_faces(StageArgs a) {
-  const int64_t g = a.f_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= a.f_end) return;
-  const Batch& b = a.b;
-  const int d = (g >= b.dir_base[2]) ? 2 : (g >= b.dir_base[1] ? 1 : 0);
-  const int64_t gl = g - b.dir_base[d];
-  const int64_t* off = b.face_off + (int64_t)d * (b.n_inst + 1);
-  const int i = find_inst(off, b.n_inst, gl);
-  if (a.check_active && !inst_active(b, i)) return;
-  const InstDesc I = b.inst[i];
-  const int64_t lf = gl - off[i];
-  const int m0 = I.n[0] + (d == 0);
-  const int m1 = I.n[1] + (d == 1);
-  int pos[3];
-  pos[0] = (int)(lf % m0);
+__device__ __forceinline__ int64_t lane_faces(const Batch& b) {
+  return b.f_count[0] + b.f_count[1] + b.f_count[2];
+}
+
+// Global face index of the t-th face of the launch's face ranges.
+__device__ __forceinline__ int64_t lane_face(const Batch& b, int64_t t) {
+  if (t < b.f_count[0]) return b.f_begin[0] + t;
+  t -= b.f_count[0];
+  if (t < b.f_count[1]) return b.f_begin[1] + t;
+  return b.f_begin[2] + (t - b.f_count[1]);
+}
+
+struct FacePos {
+  int d, i, pos[3];
+  InstDesc I;
+};
+
+__device__ __forceinline__ FacePos face_pos(const Batch& b, int64_t g) {
+  FacePos q;
+  q.d = (g >= b.dir_base[2]) ? 2 : (g >= b.dir_base[1] ? 1 : 0);
+  const int64_t gl = g - b.dir_base[q.d];
+  const int64_t* off = b.face_off + (int64_t)q.d * (b.n_inst + 1);
+  q.i = find_inst(off, b.i_begin, b.i_end, gl);
+  q.I = b.inst[q.i];
+  const int64_t lf = gl - off[q.i];
+  const int m0 = q.I.n[0] + (q.d == 0);
+  const int m1 = q.I.n[1] + (q.d == 1);
+  q.pos[0] = (int)(lf % m0);
   const int64_t r = lf / m0;
-  pos[1] = (int)(r % m1);
-  pos[2] = (int)(r / m1);
+  q.pos[1] = (int)(r % m1);
+  q.pos[2] = (int)(r / m1);
+  return q;
+}
+
+__global__ void __launch_bounds__(kFaceThreads, RR_FACE_MIN_BLOCKS) k_faces(StageArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Batch& b = a.b;
+  if (t >= lane_faces(b)) return;
+  const int64_t g = lane_face(b, t);
+  const FacePos fp = face_pos(b, g);
+  if (a.check_active && !inst_active(b, fp.i)) return;
+  const InstDesc& I = fp.I;
+  const int d = fp.d;
+  const int* pos = fp.pos;
   const int f = pos[d];
   int64_t cidx[4];
 #pragma unroll
@@ -111,7 +144,7 @@ struct CellPos {
 
 __device__ __forceinline__ CellPos cell_pos(const Batch& b, int64_t c) {
   CellPos q;
-  q.i = find_inst(b.cell_off, b.n_inst, c);
+  q.i = find_inst(b.cell_off, b.i_begin, b.i_end, c);
   q.I = b.inst[q.i];
   const int64_t lc = c - q.I.cell_off;
   q.p[0] = (int)(lc % q.I.n[0]);
@@ -184,9 +217,9 @@ __device__ __forceinline__ void store_cell(const StageArgs& a, int64_t c, const 
 }
 
 // Pass 1: every cell.  A cell whose U* is inadmissible is only flagged.
-__global__ void __launch_bounds__(kCellThreads) k_cells(StageArgs a) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= a.b.ncells) return;
+__global__ void __launch_bounds__(kCellThreads, RR_CELL_MIN_BLOCKS) k_cells(StageArgs a) {
+  const int64_t c = a.b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.b.c_end) return;
   const CellPos q = cell_pos(a.b, c);
   if (!inst_active(a.b, q.i)) return;
   double Un[NV], Vn[NV];
@@ -205,23 +238,15 @@ __global__ void __launch_bounds__(kCellThreads) k_cells(StageArgs a) {
 // Admissibility fallback, faces: first-order Rusanov flux at every face next
 // to a flagged cell.
 __global__ void __launch_bounds__(kFaceThreads) k_fallback_faces(StageArgs a) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const Batch& b = a.b;
-  if (g >= b.nfaces) return;
-  const int d = (g >= b.dir_base[2]) ? 2 : (g >= b.dir_base[1] ? 1 : 0);
-  const int64_t gl = g - b.dir_base[d];
-  const int64_t* off = b.face_off + (int64_t)d * (b.n_inst + 1);
-  const int i = find_inst(off, b.n_inst, gl);
-  if (!inst_active(b, i)) return;
-  const InstDesc I = b.inst[i];
-  const int64_t lf = gl - off[i];
-  const int m0 = I.n[0] + (d == 0);
-  const int m1 = I.n[1] + (d == 1);
-  int pos[3];
-  pos[0] = (int)(lf % m0);
-  const int64_t r = lf / m0;
-  pos[1] = (int)(r % m1);
-  pos[2] = (int)(r / m1);
+  if (t >= lane_faces(b)) return;
+  const int64_t g = lane_face(b, t);
+  const FacePos fp = face_pos(b, g);
+  if (!inst_active(b, fp.i)) return;
+  const InstDesc& I = fp.I;
+  const int d = fp.d;
+  const int* pos = fp.pos;
   int ql[3] = {pos[0], pos[1], pos[2]}, qr[3] = {pos[0], pos[1], pos[2]};
   ql[d] = map_idx(pos[d] - 1, I.n[d], I.bc[d]);
   qr[d] = map_idx(pos[d], I.n[d], I.bc[d]);
@@ -239,10 +264,10 @@ __global__ void __launch_bounds__(kFaceThreads) k_fallback_faces(StageArgs a) {
 // Admissibility fallback, cells: update again every cell with a changed face
 // (flagged, or sharing a face with a flagged cell); stage 3 also reduces the
 // next CFL signal speed of every cell and carries inactive instances over.
-__global__ void __launch_bounds__(kCellThreads) k_fallback_cells(StageArgs a) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kCellThreads, RR_CELL_MIN_BLOCKS) k_fallback_cells(StageArgs a) {
   const Batch& b = a.b;
-  if (c >= b.ncells) return;
+  const int64_t c = b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= b.c_end) return;
   const CellPos q = cell_pos(b, c);
   if (!inst_active(b, q.i)) {
     // finished or failed instance: carry its start-of-step state into the
@@ -287,9 +312,9 @@ __global__ void __launch_bounds__(kCellThreads) k_fallback_cells(StageArgs a) {
 }
 
 __global__ void k_signal(Params P, Batch b, const double* __restrict__ V) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= b.ncells) return;
-  const int i = find_inst(b.cell_off, b.n_inst, c);
+  const int64_t c = b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= b.c_end) return;
+  const int i = find_inst(b.cell_off, b.i_begin, b.i_end, c);
   const InstDesc I = b.inst[i];
   double v[NV];
   load12(V, b.ncells, c, v);
@@ -300,8 +325,8 @@ __global__ void k_signal(Params P, Batch b, const double* __restrict__ V) {
 
 // dt = CFL / max_cells sum_d lambda_d/dx_d, clipped to land on t_end.
 __global__ void k_begin_step(Params P, Batch b) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= b.n_inst) return;
+  const int i = b.i_begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.i_end) return;
   const double t = b.st.t[i], te = b.st.t_end[i];
   double dt = 0.0;
   if (b.st.status[i] == 0 && t < te) {
@@ -318,8 +343,8 @@ __global__ void k_begin_step(Params P, Batch b) {
 }
 
 __global__ void k_end_step(Batch b) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= b.n_inst) return;
+  const int i = b.i_begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.i_end) return;
   if (b.st.status[i] == 0 && b.st.dt[i] > 0.0) b.st.t[i] = b.st.t[i] + b.st.dt[i];
 }
 
@@ -385,34 +410,40 @@ inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + thread
 }  // namespace
 
 void launch_faces_f64(const StageArgs& a, cudaStream_t s) {
-  const int64_t n = a.f_end - a.f_begin;
+  const int64_t n = a.b.f_count[0] + a.b.f_count[1] + a.b.f_count[2];
   if (n <= 0) return;
   k_faces<<<grid_for(n, kFaceThreads), kFaceThreads, 0, s>>>(a);
 }
 
 void launch_cells_f64(const StageArgs& a, cudaStream_t s) {
-  if (a.b.ncells <= 0) return;
-  k_cells<<<grid_for(a.b.ncells, kCellThreads), kCellThreads, 0, s>>>(a);
+  const int64_t n = a.b.c_end - a.b.c_begin;
+  if (n <= 0) return;
+  k_cells<<<grid_for(n, kCellThreads), kCellThreads, 0, s>>>(a);
 }
 
 void launch_fallback_f64(const StageArgs& a, cudaStream_t s) {
-  if (a.b.nfaces > 0)
-    k_fallback_faces<<<grid_for(a.b.nfaces, kFaceThreads), kFaceThreads, 0, s>>>(a);
-  if (a.b.ncells > 0)
-    k_fallback_cells<<<grid_for(a.b.ncells, kCellThreads), kCellThreads, 0, s>>>(a);
+  const int64_t nf = a.b.f_count[0] + a.b.f_count[1] + a.b.f_count[2];
+  const int64_t nc = a.b.c_end - a.b.c_begin;
+  if (nf > 0) k_fallback_faces<<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(a);
+  if (nc > 0) k_fallback_cells<<<grid_for(nc, kCellThreads), kCellThreads, 0, s>>>(a);
 }
 
 void launch_signal_f64(const Params& P, const Batch& b, const double* V, cudaStream_t s) {
-  if (b.ncells <= 0) return;
-  k_signal<<<grid_for(b.ncells, 128), 128, 0, s>>>(P, b, V);
+  const int64_t n = b.c_end - b.c_begin;
+  if (n <= 0) return;
+  k_signal<<<grid_for(n, 128), 128, 0, s>>>(P, b, V);
 }
 
 void launch_begin_step(const Params& P, const Batch& b, cudaStream_t s) {
-  k_begin_step<<<grid_for(b.n_inst, 128), 128, 0, s>>>(P, b);
+  const int n = b.i_end - b.i_begin;
+  if (n <= 0) return;
+  k_begin_step<<<grid_for(n, 128), 128, 0, s>>>(P, b);
 }
 
 void launch_end_step(const Batch& b, cudaStream_t s) {
-  k_end_step<<<grid_for(b.n_inst, 128), 128, 0, s>>>(b);
+  const int n = b.i_end - b.i_begin;
+  if (n <= 0) return;
+  k_end_step<<<grid_for(n, 128), 128, 0, s>>>(b);
 }
 
 void launch_prim2con_f64(const Params& P, const double* V, double* U, int64_t n, cudaStream_t s) {

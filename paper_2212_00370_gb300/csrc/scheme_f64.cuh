@@ -273,17 +273,19 @@ __device__ __forceinline__ void picard_matrix(const ImpCell& c, const double* X,
   }
 }
 
-// Newton iteration starting from the C^(m) matrix; full forward-difference
-// Jacobian (step 1e-7 E_r) once successive steps contract by less than 4x or a
-// step gives no descent; Armijo backtracking on |R|^2; converged when the full
-// step is <= imp_tol * E_r.  Returns true on convergence.
+// Quasi-Newton iteration on R(X) = 0: first matrix C^(m) (the paper's
+// frozen-matter iteration), Broyden rank-one update after every accepted step,
+// forward-difference Jacobian (step 1e-7 E_r) when successive steps contract by
+// less than 2x or no descent is found; Armijo backtracking on |R|^2; converged
+// when the full step is <= imp_tol * E_r.  Returns true on convergence.
 static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c, double* X, double* R,
                                         double* V, double* Z) {
   double J[4][4];
-  int full = 0, jac_age = 0, need_full = 0;
+  int need_fd = 0, fresh_fd = 0, first = 1;
   double prev = -1.0;
+  picard_matrix(c, X, V, J);
   for (int m = 1; m <= P.imp_maxit; ++m) {
-    if (need_full) {
+    if (need_fd) {
       const double h = 1e-7 * X[0];
       for (int j = 0; j < 4; ++j) {
         double Xp[4] = {X[0], X[1], X[2], X[3]};
@@ -297,11 +299,9 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
 #pragma unroll
         for (int i = 0; i < 4; ++i) J[i][j] = (Rp[i] - R[i]) / dXj;
       }
-      full = 1;
-      need_full = 0;
-      jac_age = 0;
-    } else if (!full) {
-      picard_matrix(c, X, V, J);
+      need_fd = 0;
+      fresh_fd = 1;
+      first = 0;
     }
     double A[4][4], b[4], dX[4];
 #pragma unroll
@@ -310,7 +310,13 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
 #pragma unroll
       for (int j = 0; j < 4; ++j) A[i][j] = J[i][j];
     }
-    if (!solve4(A, b, dX)) return false;
+    if (!solve4(A, b, dX)) {
+      if (!fresh_fd) {
+        need_fd = 1;
+        continue;
+      }
+      return false;
+    }
 
     double dfull = 0.0;
 #pragma unroll
@@ -346,21 +352,33 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
 #pragma unroll
       for (int i = 0; i < 4; ++i) dX[i] = 0.5 * dX[i];
       lam = 0.5 * lam;
-      if (!full && k == 3) break;
+      if (first && k == 3) break;
     }
     if (!ok) {
-      if (!full || jac_age > 0) {
-        need_full = 1;
+      if (!fresh_fd) {
+        need_fd = 1;
         continue;
       }
       return false;
     }
-    jac_age++;
     double dmax = 0.0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const double dd = fabs(dX[i]);
       if (dd > dmax) dmax = dd;
+    }
+    {  // Broyden: J += (dR - J dX) dX^T / (dX . dX)
+      const double s2 = ((dX[0] * dX[0] + dX[1] * dX[1]) + dX[2] * dX[2]) + dX[3] * dX[3];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const double dRi = Rn[i] - R[i];
+        const double Jd = ((J[i][0] * dX[0] + J[i][1] * dX[1]) + J[i][2] * dX[2]) + J[i][3] * dX[3];
+        const double q = (dRi - Jd) / s2;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) J[i][j] = J[i][j] + q * dX[j];
+      }
+      fresh_fd = 0;
+      first = 0;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -370,7 +388,7 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
 #pragma unroll
     for (int k = 0; k < NV; ++k) V[k] = Vn[k];
     *Z = Zn;
-    if (prev >= 0.0 && dmax > 0.25 * prev) need_full = 1;
+    if (prev >= 0.0 && dmax > 0.5 * prev) need_fd = 1;
     prev = dmax;
   }
   return false;

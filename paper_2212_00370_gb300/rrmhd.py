@@ -30,7 +30,7 @@ class rrmhd_opts(C.Structure):
     _fields_ = [("gamma", C.c_double), ("a_rad", C.c_double), ("cfl", C.c_double),
                 ("pvm_eps", C.c_double), ("recon", C.c_int), ("beta_mode", C.c_int),
                 ("precision", C.c_int), ("c2p_maxit", C.c_int), ("imp_maxit", C.c_int),
-                ("imp_tol", C.c_double)]
+                ("imp_tol", C.c_double), ("lanes", C.c_int)]
 
 
 class RRMHDError(RuntimeError):
