@@ -45,7 +45,8 @@ typedef enum {
     RRMHD_EUNPHYS = 3,    /* inadmissible state (D <= 0, E_r <= 0, NaN speeds)  */
     RRMHD_EINVAL = 10,    /* invalid argument                                   */
     RRMHD_ENOMEM = 11,    /* device allocation failed                           */
-    RRMHD_ECUDA = 12      /* CUDA runtime error                                 */
+    RRMHD_ECUDA = 12,     /* CUDA runtime error                                 */
+    RRMHD_ECAPACITY = 13  /* input larger than an alloc-free entry point's fixed scratch */
 } rrmhd_status;
 
 enum { RRMHD_RECON_GODUNOV = 0, RRMHD_RECON_MINMOD = 1, RRMHD_RECON_MC = 2, RRMHD_RECON_VANLEER = 3 };
@@ -187,6 +188,30 @@ int rrmhd_launches_per_step(const rrmhd_ctx* ctx);
 
 /* rho h W^2 of primitives: V double[12][n] -> Z double[n] (con2prim warm starts). */
 rrmhd_status rrmhd_prim_z(rrmhd_ctx* ctx, const double* V, double* Z, int64_t n);
+
+/* ---- Alloc-free entry point (no counterpart in the paper) ----------------
+ * For callers that cannot allocate device memory themselves, e.g. a host program
+ * whose GPU memory is all owned by its own pool or fixed arena, reserved at
+ * start-up, so that no library may call cudaMalloc on its path.  It computes the
+ * CFL time step of one grid, dt = cfl / max_cells sum_d lambda_d / dx_d: the same
+ * signal speeds and the same value, bit for bit, as the time step
+ * rrmhd_imex_step takes from that state (before any clipping to t_end).
+ * grid: host, one 1D/2D/3D grid; opts: host (gamma and cfl are used); V: device
+ * double[12][ncells] primitives; dt: device double[1] output; cuda_stream: the
+ * stream to enqueue on (NULL = legacy default).  No device memory is allocated
+ * or freed: the reduction's scratch is a fixed array inside this library
+ * (about 32 KB), present on every GPU that loads the library until the process
+ * exits.  It holds up to RRMHD_NOALLOC_MAX_CELLS cells; larger grids return
+ * RRMHD_ECAPACITY before any work is enqueued.  The first call on a device looks
+ * up the scratch's device address (once per device); make that first call
+ * before any stream capture.  All calls on a device share the one scratch array
+ * (each call first resets the part that must start at zero): calls that overlap
+ * on the GPU -- on different streams, or from different host threads without
+ * ordering -- race and return wrong values.  A NaN signal speed gives dt = NaN.
+ * Returns EINVAL for bad arguments, ECUDA if the set-up or launch fails. */
+#define RRMHD_NOALLOC_MAX_CELLS 33554432
+rrmhd_status rrmhd_cfl_dt_noalloc(const rrmhd_grid* grid, const rrmhd_opts* opts, const double* V,
+                                  double* dt, void* cuda_stream);
 
 /* Text of the last error of this context (static storage owned by ctx). */
 const char* rrmhd_last_error(const rrmhd_ctx* ctx);

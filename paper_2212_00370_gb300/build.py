@@ -23,6 +23,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUD
 UNITS = {
     "rrmhd_f64.cu": ["--fmad=false"],
     "rrmhd_api.cu": [],
+    "rrmhd_noalloc.cu": ["--fmad=false"],
 }
 HEADERS = ["physics_f64.cuh", "scheme_f64.cuh", "batch.h"]
 

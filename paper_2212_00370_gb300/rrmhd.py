@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "librrmhd.so")
 RECON = {"godunov": 0, "minmod": 1, "mc": 2, "vanleer": 3}
 BC = {"outflow": 0, "periodic": 1}
 PRECISION = {"fp64": 0, "fp32_bulk": 1}
-STATUS = {0: "OK", 1: "EC2P", 2: "EIMPLICIT", 3: "EUNPHYS", 10: "EINVAL", 11: "ENOMEM", 12: "ECUDA"}
+STATUS = {0: "OK", 1: "EC2P", 2: "EIMPLICIT", 3: "EUNPHYS", 10: "EINVAL", 11: "ENOMEM", 12: "ECUDA",
+          13: "ECAPACITY"}
 
 
 class rrmhd_grid(C.Structure):
@@ -68,6 +69,7 @@ _SIGNATURES = [
     ("rrmhd_prim_z", C.c_int, [_VP, _VP, _VP, _I64]),
     ("rrmhd_profile_step", C.c_int, [_VP, _DP]),
     ("rrmhd_launches_per_step", C.c_int, [_VP]),
+    ("rrmhd_cfl_dt_noalloc", C.c_int, [C.POINTER(rrmhd_grid), C.POINTER(rrmhd_opts), _VP, _VP, _VP]),
     ("rrmhd_last_error", C.c_char_p, [_VP]),
 ]
 
