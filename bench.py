@@ -34,10 +34,10 @@ sys.path.insert(0, ROOT)
 
 # FP64-pipe instructions (DADD + DMUL + DFMA, thread level, ncu
 # sm__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum) per cell of ONE launch
-# of each kernel on this workload, measured with ncu on a 2048-instance sample of the
-# same distribution (profiles/c1_fp64_k_cells_k_faces.md).  0 = not measured for the
-# current kernel.
-FP64_INST_PER_ZONE = {"faces": 5712.0, "cells": 0.0}
+# of each kernel in the steady state of this workload (stage 1 of the 4th step),
+# measured with ncu on a 2048-instance sample of the same distribution
+# (profiles/c1_fp64_k_cells_k_faces.md).
+FP64_INST_PER_ZONE = {"faces": 5649.0, "cells": 6742.0}
 # Nominal FP64 rate of GB300: 1.25 TFLOP/s = 6.25e11 FP64-pipe instructions/s
 # (2 per SM per clock on 152 SMs at 2.07 GHz); no MEASURED_PEAKS entry exists for FP64.
 FP64_PEAK_INST = 6.25e11
