@@ -37,7 +37,10 @@ sys.path.insert(0, ROOT)
 # of each kernel in the steady state of this workload (stage 1 of the 4th step),
 # measured with ncu on a 2048-instance sample of the same distribution
 # (profiles/c1_fp64_k_cells_k_faces.md).
-FP64_INST_PER_ZONE = {"faces": 5649.0, "cells": 6742.0}
+FP64_INST_PER_ZONE = {"fp64": {"faces": 5649.0, "cells": 6742.0},
+                      "fp32_bulk": {"faces": None, "cells": None}}
+# DRAM bytes per cell of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
+TRAFFIC_PER_CELL = {"fp64": {"faces": 232.0, "cells": 541.0}, "fp32_bulk": {}}
 # Nominal FP64 rate of GB300: 1.25 TFLOP/s = 6.25e11 FP64-pipe instructions/s
 # (2 per SM per clock on 152 SMs at 2.07 GHz); no MEASURED_PEAKS entry exists for FP64.
 FP64_PEAK_INST = 6.25e11
@@ -55,6 +58,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=256, help="instances in the CPU sample")
     p.add_argument("--lanes", type=int, default=8, help="independent sub-batches (streams)")
+    p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32_bulk"],
+                   help="both: FP32-bulk is the headline value, FP64 reported beside it")
     return p.parse_args()
 
 
@@ -154,22 +159,21 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def run_ours(a, rank, world, pool, cores):
+def measure(a, precision, rank, world, local):
+    """Time K steps of the C1 batch in one precision; returns a dict of measurements."""
     import torch
     import torch.distributed as dist
 
     from paper_2212_00370_gb300 import rrmhd
     from paper_2212_00370_gb300 import workloads as W
 
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
     seed = W.SEED_BASE + 1 + rank
     w = W.riemann_batch(a.instances, seed=seed)
     grids = [rrmhd.make_grid(1, g["n"], g["dx"], g["bc"]) for g in w.grids]
-    ctx = rrmhd.Context(grids, gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl, lanes=a.lanes)
+    ctx = rrmhd.Context(grids, gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl, lanes=a.lanes,
+                        precision=precision)
     ctx.set_opacity(torch.tensor(w.kappa, device="cuda"), torch.tensor(w.sigma, device="cuda"))
-    V0 = torch.tensor(w.V, device="cuda")
-    ctx.set_state(V0)
+    ctx.set_state(torch.tensor(w.V, device="cuda"))
     ctx.set_times(np.zeros(w.n_inst), np.full(w.n_inst, np.inf))
     n_cells = np.array([g["n"][0] for g in w.grids], dtype=np.int64)
     stream = torch.cuda.current_stream()
@@ -178,12 +182,9 @@ def run_ours(a, rank, world, pool, cores):
         if world > 1:
             dist.barrier()
 
-    # warm-up (builds both step graphs)
-    ctx.imex_step(max(a.warmup, 2))
+    ctx.imex_step(max(a.warmup, 2))          # warm-up (also builds the step graphs)
     torch.cuda.synchronize()
     st_before = ctx.inst_status()
-
-    # timed region: K graph launches, per-step events on the launching stream
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
     barrier()
     torch.cuda.synchronize()
@@ -208,31 +209,29 @@ def run_ours(a, rank, world, pool, cores):
         t_s, zones = float(mx[0]), float(tt[1])
     value = zones / t_s
 
-    # per-launch-group device times of one more step (same kernels, no graph)
+    # per-launch-group device times of two more steps (same kernels, whole-batch launches)
     prof = np.zeros(4)
-    nprof = 2
-    for _ in range(nprof):
+    for _ in range(2):
         prof += ctx.profile_step()
-    prof /= nprof
+    prof /= 2
     zones_step = float(n_cells[live].sum())
-    groups = {"faces": prof[0] / 3.0, "cells": prof[1] / 3.0}   # ms per (whole-batch) launch
+    groups = {"faces": prof[0] / 3.0, "cells": prof[1] / 3.0}
+    counts = FP64_INST_PER_ZONE[precision]
     dom = max(groups, key=groups.get)
-    per_zone = FP64_INST_PER_ZONE[dom]
-    # algorithmic FP64 instructions of one launch / its duration
+    per_zone = counts.get(dom)
     achieved = per_zone * zones_step / (groups[dom] / 1e3) if per_zone else None
     roofline = {
-        "bound": "alu", "kernel": "k_" + dom + " (FP64)",
+        "bound": "alu", "kernel": ("k_%s" % dom) + (" (FP32 faces)" if precision == "fp32_bulk" and dom == "faces" else " (FP64)"),
         "achieved": achieved, "peak": FP64_PEAK_INST, "unit": "FP64-pipe inst/s",
         "frac": (achieved / FP64_PEAK_INST) if achieved else None,
-        "traffic": None,
-        "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe; no measured FP64 peak)",
+        "traffic": TRAFFIC_PER_CELL[precision].get(dom, 0) * zones_step or None,
+        "peak_source": "nominal GB300 FP64 1.25 TFLOP/s = 6.25e11 inst/s (recipe figure; "
+                       "a DFMA probe measured 5.29e11 on this pool)",
         "launch_ms": {"faces": round(groups["faces"], 4), "cells": round(groups["cells"], 4),
                       "fallback": round(prof[2] / 3.0, 4), "step_control": round(prof[3] / 2.0, 4)},
-        "faces_fp64_frac": (FP64_INST_PER_ZONE["faces"] * zones_step / (groups["faces"] / 1e3)) / FP64_PEAK_INST,
         "hbm_frac": BYTES_PER_ZONE_STEP * value / (6791.7e9),
     }
 
-    # end-to-end through the host-buffer C-ABI entry (pinned host memory)
     e2e = None
     if not a.no_e2e:
         _, Vdev = ctx.get_state()
@@ -240,7 +239,7 @@ def run_ours(a, rank, world, pool, cores):
         h_out = torch.empty(Vdev.shape, dtype=torch.float64, pin_memory=True)
         h_in.copy_(Vdev)
         torch.cuda.synchronize()
-        ctx.imex_step_host(h_in, h_out, 1)  # warm
+        ctx.imex_step_host(h_in, h_out, 1)
         ke = max(1, min(a.steps, 5))
         t0 = time.perf_counter()
         for _ in range(ke):
@@ -248,35 +247,57 @@ def run_ours(a, rank, world, pool, cores):
             h_in, h_out = h_out, h_in
         te = time.perf_counter() - t0
         st_e = ctx.inst_status()
-        zl = float(n_cells[st_e == 0].sum()) * ke
         nbytes = 12 * 8 * w.ncells
-        e2e = {"value": zl / te, "unit": "zone-updates/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": ke}
+        e2e = {"value": float(n_cells[st_e == 0].sum()) * ke / te, "unit": "zone-updates/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": ke}
+    out = {"value": value, "ms_per_step": total_ms / a.steps,
+           "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+           "roofline": roofline, "e2e": e2e, "gpu_launches": ctx.launches_per_step() * a.steps,
+           "clocks": clk.summary(), "live": int(live.sum()), "failed": int((~live).sum()),
+           "cells": int(n_cells.sum()), "ncells_state_mb": 12 * 8 * w.ncells / 1e6, "seed": seed}
+    ctx.close()
+    return out
 
+
+DTYPE = {"fp64": "f64", "fp32_bulk": "f32 faces + f64 cells"}
+
+
+def run_ours(a, rank, world, pool, cores):
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    precisions = ["fp32_bulk", "fp64"] if a.precision == "both" else [a.precision]
+    res = {p: measure(a, p, rank, world, local) for p in precisions}
+    head = res[precisions[0]]
     out = {
-        "metric": "zone-updates/s per IMEX step (FP64; % HBM roofline; p50/p99 step time)",
-        "value": value, "unit": "zone-updates/s", "n_gpus": world, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "metric": "zone-updates/s per IMEX step (FP32-bulk vs FP64, 1 GB300; % of roofline; p50/p99 step time)",
+        "value": head["value"], "unit": "zone-updates/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[precisions[0]], "data": "synthetic",
         "config": {"workload": "C1: %d independent 1D RRMHD Riemann problems per GPU, N~U{128..2048}, "
-                               "seed 2212003701+rank, gamma 4/3, PVM-int-8 + VanLeer + IMEX-RK3, FP64"
-                               % a.instances,
-                   "instances": a.instances, "cells": int(n_cells.sum()),
-                   "live_instances": int(live.sum()), "failed_instances": int((~live).sum()),
+                               "seed 2212003701+rank, gamma 4/3, PVM-int-8 + VanLeer + IMEX-RK3, "
+                               "precision %s" % (a.instances, precisions[0]),
+                   "instances": a.instances, "cells": head["cells"],
+                   "live_instances": head["live"], "failed_instances": head["failed"],
                    "parallelism": "replicas (independent problems per GPU); %d lanes (streams) per GPU" % a.lanes,
-                   "l2": "state %.0f MB per copy > 129 MB L2 (inputs larger than L2)" % (12 * 8 * w.ncells / 1e6)},
-        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
-        "roofline": roofline,
-        "e2e": e2e,
-        "gpu_launches": ctx.launches_per_step() * a.steps,
-        "clocks": clk.summary(),
+                   "l2": "state %.0f MB per copy > 129 MB L2 (inputs larger than L2)" % head["ncells_state_mb"]},
+        "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
+        "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
     }
+    if len(precisions) > 1:
+        f = res["fp64"]
+        out["fp64"] = {"value": f["value"], "ms_per_step": f["ms_per_step"], "p50_ms": f["p50_ms"],
+                       "p99_ms": f["p99_ms"], "roofline": f["roofline"], "e2e": f["e2e"],
+                       "failed_instances": f["failed"], "clocks": f["clocks"]}
+        out["fp32_bulk_speedup_over_fp64"] = head["value"] / f["value"]
+        out["gpu_launches"] += f["gpu_launches"]
     if rank == 0 and pool is not None:
-        zps, wall, zc = cpu_oracle(pool, cores, seed, a.instances, a.cpu_sample, 1)
+        zps, wall, zc = cpu_oracle(pool, cores, head["seed"], a.instances, a.cpu_sample, 1)
         out["cpu_baseline"] = {"value": zps, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
                                "sample": "%d of the %d instances (evenly spaced), 1 step each, %d zone-updates, %.1f s wall"
                                          % (a.cpu_sample, a.instances, zc, wall)}
-    ctx.close()
     return out
 
 
@@ -296,7 +317,7 @@ def run_reference(a, rank, pool, cores):
     value = zones / wall
     return {
         "impl": "reference",
-        "metric": "zone-updates/s per IMEX step (FP64; % HBM roofline; p50/p99 step time)",
+        "metric": "zone-updates/s per IMEX step (FP32-bulk vs FP64, 1 GB300; % of roofline; p50/p99 step time)",
         "value": value, "unit": "zone-updates/s", "n_gpus": 0, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1e3 * wall / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -24,8 +24,9 @@ UNITS = {
     "rrmhd_f64.cu": ["--fmad=false"],
     "rrmhd_api.cu": [],
     "rrmhd_noalloc.cu": ["--fmad=false"],
+    "rrmhd_f32.cu": [],
 }
-HEADERS = ["physics_f64.cuh", "scheme_f64.cuh", "batch.h"]
+HEADERS = ["physics_f64.cuh", "scheme_f64.cuh", "physics_f32.cuh", "batch.h", "batch_index.cuh"]
 
 
 def _deps():

@@ -60,6 +60,7 @@ struct StageArgs {
   const double* kappa;
   const double* sigma;
   double* Fhat;            // [12][fstride]; face g is stored at column g - out_base
+  float* Fhat32;           // FP32-bulk form: same layout in FP32
   int64_t fstride;
   int64_t out_base;
   int check_active;        // skip instances that are finished or failed
@@ -74,6 +75,13 @@ void launch_faces_f64(const StageArgs& a, cudaStream_t s);
 void launch_cells_f64(const StageArgs& a, cudaStream_t s);
 void launch_fallback_f64(const StageArgs& a, cudaStream_t s);
 void launch_signal_f64(const Params& P, const Batch& b, const double* V, cudaStream_t s);
+
+// FP32-bulk form: FP32 faces (tangent PVM products), FP64 cells
+void launch_faces_f32(const StageArgs& a, cudaStream_t s);
+void launch_cells_f32(const StageArgs& a, cudaStream_t s);
+void launch_fallback_f32(const StageArgs& a, cudaStream_t s);
+void launch_widen_f32(const float* F32, int64_t fstride32, int64_t f_begin, int64_t n, double* F,
+                      cudaStream_t s);
 void launch_begin_step(const Params& P, const Batch& b, cudaStream_t s);
 void launch_end_step(const Batch& b, cudaStream_t s);
 void launch_prim2con_f64(const Params& P, const double* V, double* U, int64_t n, cudaStream_t s);

@@ -1,0 +1,93 @@
+// batch_index.cuh -- integer index helpers of the packed batch layout (batch.h),
+// shared by the FP64 and FP32-bulk kernels.  No floating-point arithmetic.
+#pragma once
+#include "batch.h"
+
+namespace rr {
+namespace idx {
+
+// largest i in [lo, hi) with off[i] <= g  (off non-decreasing, off[lo] <= g)
+static __device__ __forceinline__ int find_inst(const int64_t* off, int lo, int hi, int64_t g) {
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= g)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+static __device__ __forceinline__ int map_idx(int c, int n, int bc) {
+  if (bc == 1) {
+    const int m = c % n;
+    return m < 0 ? m + n : m;
+  }
+  return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+static __device__ __forceinline__ void load12(const double* __restrict__ A, int64_t stride, int64_t c,
+                                       double* x) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) x[k] = __ldg(A + k * stride + c);
+}
+
+static __device__ __forceinline__ bool inst_active(const Batch& b, int i) {
+  return b.st.status[i] == 0 && b.st.dt[i] > 0.0;
+}
+
+static __device__ __forceinline__ int64_t lane_faces(const Batch& b) {
+  return b.f_count[0] + b.f_count[1] + b.f_count[2];
+}
+
+// Global face index of the t-th face of the launch's face ranges.
+static __device__ __forceinline__ int64_t lane_face(const Batch& b, int64_t t) {
+  if (t < b.f_count[0]) return b.f_begin[0] + t;
+  t -= b.f_count[0];
+  if (t < b.f_count[1]) return b.f_begin[1] + t;
+  return b.f_begin[2] + (t - b.f_count[1]);
+}
+
+struct FacePos {
+  int d, i, pos[3];
+  InstDesc I;
+};
+
+static __device__ __forceinline__ FacePos face_pos(const Batch& b, int64_t g) {
+  FacePos q;
+  q.d = (g >= b.dir_base[2]) ? 2 : (g >= b.dir_base[1] ? 1 : 0);
+  const int64_t gl = g - b.dir_base[q.d];
+  const int64_t* off = b.face_off + (int64_t)q.d * (b.n_inst + 1);
+  q.i = find_inst(off, b.i_begin, b.i_end, gl);
+  q.I = b.inst[q.i];
+  const int64_t lf = gl - off[q.i];
+  const int m0 = q.I.n[0] + (q.d == 0);
+  const int m1 = q.I.n[1] + (q.d == 1);
+  q.pos[0] = (int)(lf % m0);
+  const int64_t r = lf / m0;
+  q.pos[1] = (int)(r % m1);
+  q.pos[2] = (int)(r / m1);
+  return q;
+}
+
+struct CellPos {
+  int i;       // instance
+  int p[3];    // position in the instance's grid
+  InstDesc I;
+};
+
+static __device__ __forceinline__ CellPos cell_pos(const Batch& b, int64_t c) {
+  CellPos q;
+  q.i = find_inst(b.cell_off, b.i_begin, b.i_end, c);
+  q.I = b.inst[q.i];
+  const int64_t lc = c - q.I.cell_off;
+  q.p[0] = (int)(lc % q.I.n[0]);
+  const int64_t r = lc / q.I.n[0];
+  q.p[1] = (int)(r % q.I.n[1]);
+  q.p[2] = (int)(r / q.I.n[1]);
+  return q;
+}
+
+
+}  // namespace idx
+}  // namespace rr

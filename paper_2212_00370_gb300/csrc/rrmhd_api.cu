@@ -145,6 +145,7 @@ StageArgs stage_args(const rrmhd_ctx* c, const Batch& b, int stage, const double
   a.kappa = c->kappa;
   a.sigma = c->sigma;
   a.Fhat = c->Fhat;
+  a.Fhat32 = reinterpret_cast<float*>(c->Fhat);  // FP32-bulk: same buffer, FP32 entries
   a.fstride = c->nfaces;
   a.out_base = 0;
   a.check_active = 1;
@@ -153,6 +154,19 @@ StageArgs stage_args(const rrmhd_ctx* c, const Batch& b, int stage, const double
   a.cell_status = nullptr;
   a.bad = c->bad;
   return a;
+}
+
+// The three launch groups of one stage in the context's precision.
+void launch_stage(const rrmhd_ctx* c, const StageArgs& a, cudaStream_t s) {
+  if (c->opts.precision == RRMHD_FP32_BULK) {
+    rr::launch_faces_f32(a, s);
+    rr::launch_cells_f32(a, s);
+    rr::launch_fallback_f32(a, s);
+  } else {
+    rr::launch_faces_f64(a, s);
+    rr::launch_cells_f64(a, s);
+    rr::launch_fallback_f64(a, s);
+  }
 }
 
 // One IMEX-RK3 step of the instances of b, from the state in buffer set
@@ -169,11 +183,7 @@ void enqueue_step(const rrmhd_ctx* c, const Batch& b, int cur, cudaStream_t s) {
   const StageArgs s1 = stage_args(c, b, 1, AU, AV, AU, AV, BU, BV);
   const StageArgs s2 = stage_args(c, b, 2, AU, AV, BU, BV, c->Ub, c->Vb);
   const StageArgs s3 = stage_args(c, b, 3, AU, AV, c->Ub, c->Vb, BU, BV);
-  for (const StageArgs* a : {&s1, &s2, &s3}) {
-    rr::launch_faces_f64(*a, s);
-    rr::launch_cells_f64(*a, s);
-    rr::launch_fallback_f64(*a, s);
-  }
+  for (const StageArgs* a : {&s1, &s2, &s3}) launch_stage(c, *a, s);
   rr::launch_end_step(b, s);
 }
 
@@ -264,7 +274,6 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
       o.recon < 0 || o.recon > 3 || o.c2p_maxit < 1 || o.imp_maxit < 1 || !(o.imp_tol > 0.0) ||
       (o.precision != RRMHD_FP64 && o.precision != RRMHD_FP32_BULK) || o.lanes < 1)
     return RRMHD_EINVAL;
-  if (o.precision != RRMHD_FP64) return RRMHD_EINVAL;  // FP32-bulk kernels: see rrmhd_f32.cu
   std::string why;
   for (int i = 0; i < n_inst; ++i)
     if (!grid_ok(grids[i], why)) return RRMHD_EINVAL;
@@ -540,11 +549,18 @@ rrmhd_status rrmhd_flux_sweep(rrmhd_ctx* c, int dir, double* Fhat) {
   Batch b = batch_of(c);
   for (int d = 0; d < 3; ++d) b.f_count[d] = (d == dir) ? b.f_count[d] : 0;
   StageArgs a = stage_args(c, b, 0, cur_U(c), cur_V(c), cur_U(c), cur_V(c), nullptr, nullptr);
-  a.Fhat = Fhat;
-  a.fstride = c->dir_base[dir + 1] - c->dir_base[dir];
-  a.out_base = c->dir_base[dir];
   a.check_active = 0;
-  rr::launch_faces_f64(a, c->stream);
+  const int64_t nd = c->dir_base[dir + 1] - c->dir_base[dir];
+  if (c->opts.precision == RRMHD_FP32_BULK) {
+    // FP32 fluxes into the context's face buffer, widened into the caller's array
+    rr::launch_faces_f32(a, c->stream);
+    rr::launch_widen_f32(a.Fhat32, c->nfaces, c->dir_base[dir], nd, Fhat, c->stream);
+  } else {
+    a.Fhat = Fhat;
+    a.fstride = nd;
+    a.out_base = c->dir_base[dir];
+    rr::launch_faces_f64(a, c->stream);
+  }
   RR_CUDA(c, cudaGetLastError());
   return RRMHD_OK;
 }
@@ -580,12 +596,13 @@ rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
   cudaEventRecord(ev[k++], s);
   rr::launch_begin_step(c->P, b, s);
   cudaEventRecord(ev[k++], s);
+  const bool f32 = c->opts.precision == RRMHD_FP32_BULK;
   for (int i = 0; i < 3; ++i) {
-    rr::launch_faces_f64(st[i], s);
+    if (f32) rr::launch_faces_f32(st[i], s); else rr::launch_faces_f64(st[i], s);
     cudaEventRecord(ev[k++], s);
-    rr::launch_cells_f64(st[i], s);
+    if (f32) rr::launch_cells_f32(st[i], s); else rr::launch_cells_f64(st[i], s);
     cudaEventRecord(ev[k++], s);
-    rr::launch_fallback_f64(st[i], s);
+    if (f32) rr::launch_fallback_f32(st[i], s); else rr::launch_fallback_f64(st[i], s);
     cudaEventRecord(ev[k++], s);
   }
   rr::launch_end_step(b, s);

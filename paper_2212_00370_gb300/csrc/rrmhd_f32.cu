@@ -1,0 +1,254 @@
+// rrmhd_f32.cu -- kernels of the FP32-bulk form of one IMEX-RK3 stage.
+//
+// Faces (PLM, fluxes, PVM-int-8 with tangent products, the Rusanov fallback) and
+// the flux difference run in FP32; con2prim of the cells, the implicit
+// radiation-matter solve and the accumulation of U stay in FP64 (the same solver
+// as the FP64 path, compiled here with fused multiply-add).  Same launch
+// structure and lanes as rrmhd_f64.cu.
+#include <cuda_runtime.h>
+
+#include "batch.h"
+#include "batch_index.cuh"
+#include "physics_f32.cuh"
+#include "scheme_f64.cuh"
+
+namespace rr {
+
+namespace {
+using namespace idx;
+
+constexpr int kFaceThreads = 128;
+constexpr int kCellThreads = 128;
+
+__device__ __forceinline__ rr32::P32 p32_of(const Params& P) {
+  rr32::P32 q;
+  q.gamma = (float)P.gamma;
+  q.gfac = (float)P.gfac;
+  q.gm1g = (float)P.gm1g;
+  q.recon = P.recon;
+  q.beta_mode = P.beta_mode;
+  q.c2p_maxit = P.c2p_maxit;
+  return q;
+}
+
+__device__ __forceinline__ void load12f(const double* __restrict__ A, int64_t stride, int64_t c,
+                                        float* x) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) x[k] = (float)__ldg(A + k * stride + c);
+}
+
+__global__ void __launch_bounds__(kFaceThreads) k_faces_f32(StageArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Batch& b = a.b;
+  if (t >= lane_faces(b)) return;
+  const int64_t g = lane_face(b, t);
+  const FacePos fp = face_pos(b, g);
+  if (a.check_active && !inst_active(b, fp.i)) return;
+  const InstDesc& I = fp.I;
+  const int d = fp.d;
+  const int f = fp.pos[d];
+  int64_t cidx[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    int q[3] = {fp.pos[0], fp.pos[1], fp.pos[2]};
+    q[d] = map_idx(f - 2 + s, I.n[d], I.bc[d]);
+    cidx[s] = I.cell_off + ((int64_t)q[2] * I.n[1] + q[1]) * I.n[0] + q[0];
+  }
+  const rr32::P32 P = p32_of(a.P);
+  const int64_t N = b.ncells;
+  float VL[NV], VR[NV];
+  {
+    float w0[NV], w1[NV], w2[NV], tmp[NV];
+    load12f(a.Vs, N, cidx[0], w0);
+    load12f(a.Vs, N, cidx[1], w1);
+    load12f(a.Vs, N, cidx[2], w2);
+    rr32::reconstruct(P.recon, w0, w1, w2, tmp, VL);
+    load12f(a.Vs, N, cidx[3], w0);
+    rr32::reconstruct(P.recon, w1, w2, w0, VR, tmp);
+  }
+  const float dxd = (float)I.dx[d];
+  const float tauL = (float)(__ldg(a.Us + cidx[1]) * (__ldg(a.kappa + cidx[1]) + __ldg(a.sigma + cidx[1]))) * dxd;
+  const float tauR = (float)(__ldg(a.Us + cidx[2]) * (__ldg(a.kappa + cidx[2]) + __ldg(a.sigma + cidx[2]))) * dxd;
+  float F[NV];
+  rr32::pvm_flux(P, d, VL, VR, tauL, tauR, F);
+  const int64_t o = g - a.out_base;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) a.Fhat32[k * a.fstride + o] = F[k];
+}
+
+// U* with the flux difference in FP32, accumulated into FP64; FP64 implicit solve.
+__device__ __forceinline__ int cell_update_f32(const StageArgs& a, int64_t c, const CellPos& q,
+                                               double* Un, double* Vn) {
+  const Batch& b = a.b;
+  const InstDesc& I = q.I;
+  const double dt = b.st.dt[q.i];
+  float dtdx[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dtdx[d] = (float)(dt / I.dx[d]);
+  int64_t fl[3], fr[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int m0 = I.n[0] + (d == 0);
+    const int m1 = I.n[1] + (d == 1);
+    const int64_t base = b.dir_base[d] + b.face_off[(int64_t)d * (b.n_inst + 1) + q.i];
+    fl[d] = base + ((int64_t)q.p[2] * m1 + q.p[1]) * m0 + q.p[0];
+    int r[3] = {q.p[0], q.p[1], q.p[2]};
+    r[d] += 1;
+    fr[d] = base + ((int64_t)r[2] * m1 + r[1]) * m0 + r[0];
+  }
+  double ca = 0.0, cb = 1.0, cw = 1.0;
+  if (a.stage == 2) {
+    ca = 0.75;
+    cb = 0.25;
+    cw = 0.25;
+  } else if (a.stage == 3) {
+    ca = 1.0 / 3.0;
+    cb = 2.0 / 3.0;
+    cw = 2.0 / 3.0;
+  }
+  const int64_t N = b.ncells;
+  const int64_t FS = a.fstride;
+  double Ust[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    float acc = (a.Fhat32[k * FS + fr[0]] - a.Fhat32[k * FS + fl[0]]) * dtdx[0];
+    for (int d = 1; d < I.ndim; ++d) acc += (a.Fhat32[k * FS + fr[d]] - a.Fhat32[k * FS + fl[d]]) * dtdx[d];
+    const double us = a.Us[k * N + c];
+    Ust[k] = (a.stage == 1) ? us - (double)acc : ca * a.U0[k * N + c] + cb * (us - (double)acc);
+  }
+  double vs[NV];
+  load12(a.Vs, N, c, vs);
+  return implicit_cell(a.P, a.kappa[c], a.sigma[c], cw * dt, Ust, prim_Z(a.P, vs), Un, Vn);
+}
+
+__device__ __forceinline__ void store_cell(const StageArgs& a, int64_t c, const double* Un,
+                                           const double* Vn) {
+  const int64_t N = a.b.ncells;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    a.Uout[k * N + c] = Un[k];
+    a.Vout[k * N + c] = Vn[k];
+  }
+}
+
+__global__ void __launch_bounds__(kCellThreads) k_cells_f32(StageArgs a) {
+  const int64_t c = a.b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.b.c_end) return;
+  const CellPos q = cell_pos(a.b, c);
+  if (!inst_active(a.b, q.i)) return;
+  double Un[NV], Vn[NV];
+  const int rc = cell_update_f32(a, c, q, Un, Vn);
+  if (a.cell_status) a.cell_status[c] = rc;
+  const bool inadmissible = (rc == ST_C2P || rc == ST_UNPHYS);
+  a.bad[c] = inadmissible ? 1 : 0;
+  if (inadmissible) return;
+  if (rc != ST_OK) {
+    atomicCAS(a.b.st.status + q.i, 0, rc);
+    return;
+  }
+  store_cell(a, c, Un, Vn);
+}
+
+__global__ void __launch_bounds__(kFaceThreads) k_fallback_faces_f32(StageArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Batch& b = a.b;
+  if (t >= lane_faces(b)) return;
+  const int64_t g = lane_face(b, t);
+  const FacePos fp = face_pos(b, g);
+  if (!inst_active(b, fp.i)) return;
+  const InstDesc& I = fp.I;
+  const int d = fp.d;
+  int ql[3] = {fp.pos[0], fp.pos[1], fp.pos[2]}, qr[3] = {fp.pos[0], fp.pos[1], fp.pos[2]};
+  ql[d] = map_idx(fp.pos[d] - 1, I.n[d], I.bc[d]);
+  qr[d] = map_idx(fp.pos[d], I.n[d], I.bc[d]);
+  const int64_t cl = I.cell_off + ((int64_t)ql[2] * I.n[1] + ql[1]) * I.n[0] + ql[0];
+  const int64_t cr = I.cell_off + ((int64_t)qr[2] * I.n[1] + qr[1]) * I.n[0] + qr[0];
+  if (!a.bad[cl] && !a.bad[cr]) return;
+  float vl[NV], vr[NV], F[NV];
+  load12f(a.Vs, b.ncells, cl, vl);
+  load12f(a.Vs, b.ncells, cr, vr);
+  rr32::llf_flux(p32_of(a.P), d, vl, vr, F);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) a.Fhat32[k * a.fstride + g] = F[k];
+}
+
+__global__ void __launch_bounds__(kCellThreads) k_fallback_cells_f32(StageArgs a) {
+  const Batch& b = a.b;
+  const int64_t c = b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= b.c_end) return;
+  const CellPos q = cell_pos(b, c);
+  if (!inst_active(b, q.i)) {
+    if (a.stage == 3) {
+      double u[NV], v[NV];
+      load12(a.U0, b.ncells, c, u);
+      load12(a.V0, b.ncells, c, v);
+      store_cell(a, c, u, v);
+    }
+    return;
+  }
+  const InstDesc& I = q.I;
+  bool hit = a.bad[c] != 0;
+  for (int d = 0; d < I.ndim && !hit; ++d) {
+    for (int e = -1; e <= 1; e += 2) {
+      const int pd = q.p[d] + e;
+      if ((pd < 0 || pd >= I.n[d]) && I.bc[d] != 1) continue;
+      int r[3] = {q.p[0], q.p[1], q.p[2]};
+      r[d] = map_idx(pd, I.n[d], I.bc[d]);
+      if (a.bad[I.cell_off + ((int64_t)r[2] * I.n[1] + r[1]) * I.n[0] + r[0]]) hit = true;
+    }
+  }
+  double Vn[NV];
+  if (hit) {
+    double Un[NV];
+    const int rc = cell_update_f32(a, c, q, Un, Vn);
+    if (a.cell_status) a.cell_status[c] = rc;
+    if (rc != ST_OK) {
+      atomicCAS(b.st.status + q.i, 0, rc);
+      return;
+    }
+    store_cell(a, c, Un, Vn);
+  } else if (a.stage == 3) {
+    load12(a.Vout, b.ncells, c, Vn);
+  }
+  if (a.stage == 3) {
+    double s = signal_speed(a.P, 0, Vn) / I.dx[0];
+    for (int d = 1; d < I.ndim; ++d) s = s + signal_speed(a.P, d, Vn) / I.dx[d];
+    atomicMax(b.st.smax + q.i, (unsigned long long)__double_as_longlong(s));
+  }
+}
+
+__global__ void k_widen(const float* __restrict__ F32, int64_t fs32, int64_t f_begin, int64_t n,
+                        double* __restrict__ F) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) F[k * n + t] = (double)F32[k * fs32 + f_begin + t];
+}
+
+inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+void launch_faces_f32(const StageArgs& a, cudaStream_t s) {
+  const int64_t n = a.b.f_count[0] + a.b.f_count[1] + a.b.f_count[2];
+  if (n > 0) k_faces_f32<<<grid_for(n, kFaceThreads), kFaceThreads, 0, s>>>(a);
+}
+
+void launch_cells_f32(const StageArgs& a, cudaStream_t s) {
+  const int64_t n = a.b.c_end - a.b.c_begin;
+  if (n > 0) k_cells_f32<<<grid_for(n, kCellThreads), kCellThreads, 0, s>>>(a);
+}
+
+void launch_fallback_f32(const StageArgs& a, cudaStream_t s) {
+  const int64_t nf = a.b.f_count[0] + a.b.f_count[1] + a.b.f_count[2];
+  const int64_t nc = a.b.c_end - a.b.c_begin;
+  if (nf > 0) k_fallback_faces_f32<<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(a);
+  if (nc > 0) k_fallback_cells_f32<<<grid_for(nc, kCellThreads), kCellThreads, 0, s>>>(a);
+}
+
+void launch_widen_f32(const float* F32, int64_t fstride32, int64_t f_begin, int64_t n, double* F,
+                      cudaStream_t s) {
+  if (n > 0) k_widen<<<grid_for(n, 256), 256, 0, s>>>(F32, fstride32, f_begin, n, F);
+}
+
+}  // namespace rr

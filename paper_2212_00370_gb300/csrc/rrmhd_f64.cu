@@ -16,11 +16,13 @@
 #include <cuda_runtime.h>
 
 #include "batch.h"
+#include "batch_index.cuh"
 #include "scheme_f64.cuh"
 
 namespace rr {
 
 namespace {
+using namespace idx;
 
 constexpr int kFaceThreads = 128;
 constexpr int kCellThreads = 128;
@@ -32,70 +34,6 @@ constexpr int kCellThreads = 128;
 #ifndef RR_CELL_MIN_BLOCKS
 #define RR_CELL_MIN_BLOCKS 1
 #endif
-
-// largest i in [lo, hi) with off[i] <= g  (off non-decreasing, off[lo] <= g)
-__device__ __forceinline__ int find_inst(const int64_t* off, int lo, int hi, int64_t g) {
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (off[mid] <= g)
-      lo = mid;
-    else
-      hi = mid;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ int map_idx(int c, int n, int bc) {
-  if (bc == 1) {
-    const int m = c % n;
-    return m < 0 ? m + n : m;
-  }
-  return c < 0 ? 0 : (c >= n ? n - 1 : c);
-}
-
-__device__ __forceinline__ void load12(const double* __restrict__ A, int64_t stride, int64_t c,
-                                       double* x) {
-#pragma unroll
-  for (int k = 0; k < NV; ++k) x[k] = __ldg(A + k * stride + c);
-}
-
-__device__ __forceinline__ bool inst_active(const Batch& b, int i) {
-  return b.st.status[i] == 0 && b.st.dt[i] > 0.0;
-}
-
-__device__ __forceinline__ int64_t lane_faces(const Batch& b) {
-  return b.f_count[0] + b.f_count[1] + b.f_count[2];
-}
-
-// Global face index of the t-th face of the launch's face ranges.
-__device__ __forceinline__ int64_t lane_face(const Batch& b, int64_t t) {
-  if (t < b.f_count[0]) return b.f_begin[0] + t;
-  t -= b.f_count[0];
-  if (t < b.f_count[1]) return b.f_begin[1] + t;
-  return b.f_begin[2] + (t - b.f_count[1]);
-}
-
-struct FacePos {
-  int d, i, pos[3];
-  InstDesc I;
-};
-
-__device__ __forceinline__ FacePos face_pos(const Batch& b, int64_t g) {
-  FacePos q;
-  q.d = (g >= b.dir_base[2]) ? 2 : (g >= b.dir_base[1] ? 1 : 0);
-  const int64_t gl = g - b.dir_base[q.d];
-  const int64_t* off = b.face_off + (int64_t)q.d * (b.n_inst + 1);
-  q.i = find_inst(off, b.i_begin, b.i_end, gl);
-  q.I = b.inst[q.i];
-  const int64_t lf = gl - off[q.i];
-  const int m0 = q.I.n[0] + (q.d == 0);
-  const int m1 = q.I.n[1] + (q.d == 1);
-  q.pos[0] = (int)(lf % m0);
-  const int64_t r = lf / m0;
-  q.pos[1] = (int)(r % m1);
-  q.pos[2] = (int)(r / m1);
-  return q;
-}
 
 __global__ void __launch_bounds__(kFaceThreads, RR_FACE_MIN_BLOCKS) k_faces(StageArgs a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -134,24 +72,6 @@ __global__ void __launch_bounds__(kFaceThreads, RR_FACE_MIN_BLOCKS) k_faces(Stag
   const int64_t o = g - a.out_base;
 #pragma unroll
   for (int k = 0; k < NV; ++k) a.Fhat[k * a.fstride + o] = F[k];
-}
-
-struct CellPos {
-  int i;       // instance
-  int p[3];    // position in the instance's grid
-  InstDesc I;
-};
-
-__device__ __forceinline__ CellPos cell_pos(const Batch& b, int64_t c) {
-  CellPos q;
-  q.i = find_inst(b.cell_off, b.i_begin, b.i_end, c);
-  q.I = b.inst[q.i];
-  const int64_t lc = c - q.I.cell_off;
-  q.p[0] = (int)(lc % q.I.n[0]);
-  const int64_t r = lc / q.I.n[0];
-  q.p[1] = (int)(r % q.I.n[1]);
-  q.p[2] = (int)(r / q.I.n[1]);
-  return q;
 }
 
 // U* of cell c from its face fluxes (flux difference and RK combination,
