@@ -37,10 +37,11 @@ sys.path.insert(0, ROOT)
 # of each kernel in the steady state of this workload (stage 1 of the 4th step),
 # measured with ncu on a 2048-instance sample of the same distribution
 # (profiles/c1_fp64_k_cells_k_faces.md).
-FP64_INST_PER_ZONE = {"fp64": {"faces": 5649.0, "cells": 6742.0},
-                      "fp32_bulk": {"faces": None, "cells": None}}
+FP64_INST_PER_ZONE = {"fp64": {"faces": 5640.0, "cells": 5439.0},
+                      "fp32_bulk": {"faces": None, "cells": 4299.0}}
 # DRAM bytes per cell of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
-TRAFFIC_PER_CELL = {"fp64": {"faces": 232.0, "cells": 541.0}, "fp32_bulk": {}}
+TRAFFIC_PER_CELL = {"fp64": {"faces": 240.0, "cells": 1033.0},
+                    "fp32_bulk": {"faces": 167.0, "cells": 935.0}}
 # Nominal FP64 rate of GB300: 1.25 TFLOP/s = 6.25e11 FP64-pipe instructions/s
 # (2 per SM per clock on 152 SMs at 2.07 GHz); no MEASURED_PEAKS entry exists for FP64.
 FP64_PEAK_INST = 6.25e11

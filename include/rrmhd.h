@@ -74,7 +74,7 @@ typedef struct {
     int    precision;  /* RRMHD_FP64 (reproducible) or RRMHD_FP32_BULK                     */
     int    c2p_maxit;  /* Newton iterations allowed in con2prim (60)                       */
     int    imp_maxit;  /* iterations allowed in one implicit Newton solve (50)             */
-    double imp_tol;    /* implicit convergence: full Newton step <= imp_tol * E_r (1e-12)  */
+    double imp_tol;    /* implicit convergence: full Newton step <= imp_tol * E_r (1e-10)  */
     int    lanes;      /* independent sub-batches stepped on their own streams (8); the
                           instances are split into contiguous ranges of about equal cell
                           count, so one range's slow cells overlap the others' work     */

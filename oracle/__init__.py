@@ -61,7 +61,7 @@ class Params:
     implicit: str = "newton"
     c2p_maxit: int = 60
     imp_maxit: int = 50
-    imp_tol: float = 1e-12
+    imp_tol: float = 1e-10
 
     def struct(self):
         p = _Params(self.gamma, self.a_rad, self.cfl, self.pvm_eps, RECON[self.recon],
@@ -124,6 +124,7 @@ def lib():
             "or_grid_stage": (C.c_int, [P, G, C.c_int, C.c_double, dp, dp, dp, dp, dp, dp, dp,
                                         i32p, S]),
             "or_grid_step": (C.c_int, [P, G, C.c_double, dp, dp, dp, dp, S]),
+            "or_grid_step_c": (C.c_int, [P, G, C.c_double, dp, dp, dp, dp, dp, S]),
             "or_grid_run": (C.c_int, [P, G, C.c_double, C.c_double, C.c_int, dp, dp, dp, dp,
                                       dp, C.POINTER(C.c_int), S]),
         }
@@ -330,15 +331,20 @@ def stage(g, s, dt, U0, Us, Vs, kappa, sigma, P, stats=None):
     return Uo, Vo, cs, nf
 
 
-def step(g, dt, U, V, kappa, sigma, P, stats=None):
-    """One IMEX-RK3 step in place; returns the number of failed cells."""
+def step(g, dt, U, V, kappa, sigma, P, stats=None, jcache=None):
+    """One IMEX-RK3 step in place; returns the number of failed cells.  jcache: a
+    float64 array of 17 * ncells (zeros = empty) carried between steps, or None."""
     N = g.ncells
     assert U.flags.c_contiguous and V.flags.c_contiguous and U.dtype == np.float64
     k = np.ascontiguousarray(kappa, dtype=np.float64).reshape(-1)
     s = np.ascontiguousarray(sigma, dtype=np.float64).reshape(-1)
     assert U.size == 12 * N
-    return lib().or_grid_step(C.byref(P.struct()), C.byref(g.struct()), float(dt), _d(U), _d(V),
-                              _d(k), _d(s), _stats(stats))
+    if jcache is None:
+        return lib().or_grid_step(C.byref(P.struct()), C.byref(g.struct()), float(dt), _d(U),
+                                  _d(V), _d(k), _d(s), _stats(stats))
+    assert jcache.size == 17 * N and jcache.dtype == np.float64 and jcache.flags.c_contiguous
+    return lib().or_grid_step_c(C.byref(P.struct()), C.byref(g.struct()), float(dt), _d(U),
+                                _d(V), _d(k), _d(s), _d(jcache), _stats(stats))
 
 
 def run(g, t0, t_end, U, V, kappa, sigma, P, max_steps=10 ** 9, stats=None):

@@ -107,6 +107,7 @@ typedef struct {
     double* Fh[3];
     int m[3][3];
     const double *U0, *Us, *Vs, *kappa, *sigma;
+    double* jc;   /* per-cell Jacobian cache, [17][N] planes, or NULL */
 } stage_ctx;
 
 /* U* of one cell from its face fluxes, then the implicit solve (Sec. 3.3). */
@@ -136,7 +137,12 @@ static int cell_update(const stage_ctx* s, int i, int j, int k, double Un[12], d
     }
     load(s->Vs, N, c, vs);
     double Zg = or_prim_Z(s->P, vs);
-    return or_implicit(s->P, s->kappa[c], s->sigma[c], s->hdt, Ust, Zg, Un, Vn, st);
+    if (!s->jc) return or_implicit(s->P, s->kappa[c], s->sigma[c], s->hdt, Ust, Zg, Un, Vn, st);
+    double jc[17];
+    for (int q = 0; q < 17; q++) jc[q] = s->jc[q * N + c];
+    int rc = or_implicit_c(s->P, s->kappa[c], s->sigma[c], s->hdt, Ust, Zg, Un, Vn, jc, st);
+    for (int q = 0; q < 17; q++) s->jc[q * N + c] = jc[q];
+    return rc;
 }
 
 static int inadmissible(int rc) { return rc == OR_EC2P || rc == OR_EUNPHYS; }
@@ -152,13 +158,14 @@ static int inadmissible(int rc) { return rc == OR_EC2P || rc == OR_EUNPHYS; }
  * first-order lambda_max = 1 Rusanov flux of the cell-centre states
  * (or_llf_flux), and all cells touching such a face are updated again.  A cell
  * that still fails counts as failed.  Uout/Vout must not alias the inputs. */
-int or_grid_stage(const or_params* P, const or_grid* g, int stage, double dt,
-                  const double* U0, const double* Us, const double* Vs,
-                  const double* kappa, const double* sigma,
-                  double* Uout, double* Vout, int32_t* cell_status, or_stats* st)
+int or_grid_stage_c(const or_params* P, const or_grid* g, int stage, double dt,
+                    const double* U0, const double* Us, const double* Vs,
+                    const double* kappa, const double* sigma,
+                    double* Uout, double* Vout, int32_t* cell_status, double* jcache, or_stats* st)
 {
     int64_t N = ncells(g);
     stage_ctx s;
+    s.jc = jcache;
     s.P = P;
     s.g = g;
     s.stage = stage;
@@ -257,9 +264,18 @@ int or_grid_stage(const or_params* P, const or_grid* g, int stage, double dt,
     return nfail;
 }
 
-/* One full IMEX-RK3 step of size dt; U and V are updated in place. */
-int or_grid_step(const or_params* P, const or_grid* g, double dt, double* U, double* V,
-                 const double* kappa, const double* sigma, or_stats* st)
+int or_grid_stage(const or_params* P, const or_grid* g, int stage, double dt,
+                  const double* U0, const double* Us, const double* Vs,
+                  const double* kappa, const double* sigma,
+                  double* Uout, double* Vout, int32_t* cell_status, or_stats* st)
+{
+    return or_grid_stage_c(P, g, stage, dt, U0, Us, Vs, kappa, sigma, Uout, Vout, cell_status, 0, st);
+}
+
+/* One full IMEX-RK3 step of size dt; U and V are updated in place.  jcache: the
+ * per-cell Jacobian cache carried from step to step ([17][N], zero = empty), or NULL. */
+int or_grid_step_c(const or_params* P, const or_grid* g, double dt, double* U, double* V,
+                   const double* kappa, const double* sigma, double* jcache, or_stats* st)
 {
     int64_t N = ncells(g);
     size_t bytes = sizeof(double) * 12 * (size_t)N;
@@ -268,9 +284,9 @@ int or_grid_step(const or_params* P, const or_grid* g, double dt, double* U, dou
     double* U2 = (double*)malloc(bytes);
     double* V2 = (double*)malloc(bytes);
     int nfail = 0;
-    nfail += or_grid_stage(P, g, 1, dt, U, U, V, kappa, sigma, U1, V1, 0, st);
-    if (!nfail) nfail += or_grid_stage(P, g, 2, dt, U, U1, V1, kappa, sigma, U2, V2, 0, st);
-    if (!nfail) nfail += or_grid_stage(P, g, 3, dt, U, U2, V2, kappa, sigma, U1, V1, 0, st);
+    nfail += or_grid_stage_c(P, g, 1, dt, U, U, V, kappa, sigma, U1, V1, 0, jcache, st);
+    if (!nfail) nfail += or_grid_stage_c(P, g, 2, dt, U, U1, V1, kappa, sigma, U2, V2, 0, jcache, st);
+    if (!nfail) nfail += or_grid_stage_c(P, g, 3, dt, U, U2, V2, kappa, sigma, U1, V1, 0, jcache, st);
     if (!nfail) {
         memcpy(U, U1, bytes);
         memcpy(V, V1, bytes);
@@ -282,14 +298,22 @@ int or_grid_step(const or_params* P, const or_grid* g, double dt, double* U, dou
     return nfail;
 }
 
+int or_grid_step(const or_params* P, const or_grid* g, double dt, double* U, double* V,
+                 const double* kappa, const double* sigma, or_stats* st)
+{
+    return or_grid_step_c(P, g, dt, U, V, kappa, sigma, 0, st);
+}
+
 /* Advance from t0 to t_end (the last step is clipped to land on t_end), at
- * most max_steps steps.  Returns the number of failed cells (0 on success). */
+ * most max_steps steps, with a per-cell Jacobian cache that starts empty.
+ * Returns the number of failed cells (0 on success). */
 int or_grid_run(const or_params* P, const or_grid* g, double t0, double t_end, int max_steps,
                 double* U, double* V, const double* kappa, const double* sigma,
                 double* t_out, int* steps_out, or_stats* st)
 {
     double t = t0;
     int s = 0, nfail = 0;
+    double* jc = (double*)calloc((size_t)17 * ncells(g), sizeof(double));
     while (t < t_end && s < max_steps) {
         double dt = or_grid_dt(P, g, V);
         if (t + dt > t_end) dt = t_end - t;
@@ -297,11 +321,12 @@ int or_grid_run(const or_params* P, const or_grid* g, double t0, double t_end, i
             nfail = 1;
             break;
         }
-        nfail = or_grid_step(P, g, dt, U, V, kappa, sigma, st);
+        nfail = or_grid_step_c(P, g, dt, U, V, kappa, sigma, jc, st);
         if (nfail) break;
         t = t + dt;
         s++;
     }
+    free(jc);
     if (t_out) *t_out = t;
     if (steps_out) *steps_out = s;
     return nfail;

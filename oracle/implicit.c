@@ -189,15 +189,22 @@ static void picard_jacobian(const imp_ctx* c, const double X[4], const double V[
  * forward-difference Jacobian (step 1e-7 E_r).  Every step is damped by a
  * backtracking line search on |R|^2 (Armijo 1e-4); converged when the full step
  * is <= imp_tol * E_r. */
-static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z)
+static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z,
+                  const double* Min, double* Mout)
 {
     const or_params* P = c->P;
     double J[4][4];
     int need_fd = 0;      /* replace J by a forward-difference Jacobian          */
     int fresh_fd = 0;     /* J is an FD Jacobian at the current X, not updated   */
-    int first = 1;        /* J is the initial frozen-matter matrix C^(m)         */
+    int first = 1;        /* J is the initial matrix (C^(m) or the cached one)   */
     double prev = -1.0;
-    picard_jacobian(c, X, V, J);
+    if (Min) {
+        /* the cell's matrix from its previous solve: J = I + h M */
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 4; j++) J[i][j] = (i == j ? 1.0 : 0.0) + c->hdt * Min[4 * i + j];
+    } else {
+        picard_jacobian(c, X, V, J);
+    }
     for (int m = 1; m <= P->imp_maxit; m++) {
         if (need_fd) {
             double h = 1e-7 * X[0];
@@ -241,6 +248,10 @@ static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z)
             }
             for (int k = 0; k < 12; k++) V[k] = Vn[k];
             *Z = Zn;
+            if (Mout)
+                for (int i = 0; i < 4; i++)
+                    for (int j = 0; j < 4; j++)
+                        Mout[4 * i + j] = (J[i][j] - (i == j ? 1.0 : 0.0)) / c->hdt;
             return 0;
         }
         /* backtracking line search: halve the step until the matter state is
@@ -294,8 +305,14 @@ static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z)
     return 1;
 }
 
-int or_implicit(const or_params* P, double kappa, double sigma, double hdt,
-                const double Ustar[12], double Zguess, double U[12], double V[12], or_stats* st)
+/* jc (may be NULL): the cell's Jacobian cache, 16 entries of M = (J - I)/h from its
+ * last converged solve and a validity flag jc[16].  A valid entry is the first
+ * matrix of the quasi-Newton iteration instead of C^(m); the converged matrix is
+ * stored back (the flag is cleared when the solve fails).  M does not depend on h,
+ * so it carries over between stages of different weight. */
+int or_implicit_c(const or_params* P, double kappa, double sigma, double hdt,
+                  const double Ustar[12], double Zguess, double U[12], double V[12], double* jc,
+                  or_stats* st)
 {
     if (st) st->imp_cells++;
     if ((kappa == 0.0 && sigma == 0.0) || hdt == 0.0) {
@@ -329,7 +346,8 @@ int or_implicit(const or_params* P, double kappa, double sigma, double hdt,
     if (P->imp_mode == OR_IMP_PICARD) {
         fail = picard(&c, X, V, &Z);
     } else {
-        fail = newton(&c, X, R, V, &Z);
+        double Mnew[16];
+        fail = newton(&c, X, R, V, &Z, (jc && jc[16] != 0.0) ? jc : 0, Mnew);
         if (fail) {
             /* continuation in the implicit weight: solve with h/64, h/32, ..., h,
              * each from the previous solution (the solution moves continuously
@@ -340,9 +358,13 @@ int or_implicit(const or_params* P, double kappa, double sigma, double hdt,
             for (int j = IMP_LADDER; j >= 0 && !fail; j--) {
                 c.hdt = hdt / (double)(1 << j);
                 fail = imp_residual(&c, X, Z, R, V, &Z);
-                if (!fail) fail = newton(&c, X, R, V, &Z);
+                if (!fail) fail = newton(&c, X, R, V, &Z, 0, Mnew);
             }
             c.hdt = hdt;
+        }
+        if (jc) {
+            for (int k = 0; k < 16; k++) jc[k] = fail ? 0.0 : Mnew[k];
+            jc[16] = fail ? 0.0 : 1.0;
         }
     }
     if (fail) {
@@ -351,6 +373,12 @@ int or_implicit(const or_params* P, double kappa, double sigma, double hdt,
     }
     matter_state(&c, X, U);
     return OR_OK;
+}
+
+int or_implicit(const or_params* P, double kappa, double sigma, double hdt,
+                const double Ustar[12], double Zguess, double U[12], double V[12], or_stats* st)
+{
+    return or_implicit_c(P, kappa, sigma, hdt, Ustar, Zguess, U, V, 0, st);
 }
 
 void or_implicit_n(const or_params* P, int64_t n, const double* kappa, const double* sigma,

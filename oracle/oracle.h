@@ -91,6 +91,9 @@ void   or_llf_flux(const or_params* P, int dir, const double VL[12], const doubl
 /* ---- implicit step (implicit.c) ---- */
 int  or_implicit(const or_params* P, double kappa, double sigma, double hdt,
                  const double Ustar[12], double Zguess, double U[12], double V[12], or_stats* st);
+int  or_implicit_c(const or_params* P, double kappa, double sigma, double hdt,
+                   const double Ustar[12], double Zguess, double U[12], double V[12], double* jc,
+                   or_stats* st);
 void or_picard_matrix(double kappa, double sigma, double hdt, double rho, const double u[3],
                       double W, double BP, const double Dr[3][3],
                       const double Ustar_r[4], double C[4][4], double rhs[4]);
@@ -114,6 +117,13 @@ int    or_grid_stage(const or_params* P, const or_grid* g, int stage, double dt,
                      double* Uout, double* Vout, int32_t* cell_status, or_stats* st);
 int    or_grid_step(const or_params* P, const or_grid* g, double dt, double* U, double* V,
                     const double* kappa, const double* sigma, or_stats* st);
+int    or_grid_stage_c(const or_params* P, const or_grid* g, int stage, double dt,
+                       const double* U0, const double* Us, const double* Vs,
+                       const double* kappa, const double* sigma,
+                       double* Uout, double* Vout, int32_t* cell_status, double* jcache,
+                       or_stats* st);
+int    or_grid_step_c(const or_params* P, const or_grid* g, double dt, double* U, double* V,
+                      const double* kappa, const double* sigma, double* jcache, or_stats* st);
 int    or_grid_run(const or_params* P, const or_grid* g, double t0, double t_end, int max_steps,
                    double* U, double* V, const double* kappa, const double* sigma,
                    double* t_out, int* steps_out, or_stats* st);

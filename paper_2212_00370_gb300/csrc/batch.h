@@ -68,6 +68,7 @@ struct StageArgs {
   double* Vout;
   int32_t* cell_status;    // optional per-cell status
   uint8_t* bad;            // [ncells] cells whose U* is inadmissible (admissibility fallback)
+  double* jc;              // [17][ncells] per-cell Jacobian cache of the implicit solve
 };
 
 // FP64 path (bit-compatible with the oracle's arithmetic order)

@@ -44,6 +44,7 @@ struct rrmhd_ctx {
   double *V0 = nullptr, *Va = nullptr, *Vb = nullptr;
   double *kappa = nullptr, *sigma = nullptr, *Fhat = nullptr;
   uint8_t* bad = nullptr;  // admissibility-fallback flags, one per cell
+  double* jc = nullptr;    // per-cell Jacobian cache of the implicit solve, [17][ncells]
   int cur = 0;             // the state lives in (U0,V0) when 0, in (Ua,Va) when 1
   double *t = nullptr, *t_end = nullptr, *dt = nullptr;
   unsigned long long* smax = nullptr;
@@ -153,6 +154,7 @@ StageArgs stage_args(const rrmhd_ctx* c, const Batch& b, int stage, const double
   a.Vout = Vout;
   a.cell_status = nullptr;
   a.bad = c->bad;
+  a.jc = c->jc;
   return a;
 }
 
@@ -239,7 +241,7 @@ void rrmhd_default_opts(rrmhd_opts* o) {
   o->precision = RRMHD_FP64;
   o->c2p_maxit = 60;
   o->imp_maxit = 50;
-  o->imp_tol = 1e-12;
+  o->imp_tol = 1e-10;
   o->lanes = 8;
 }
 
@@ -258,7 +260,7 @@ void rrmhd_destroy(rrmhd_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* bufs[] = {c->d_inst, c->d_cell_off, c->d_face_off, c->U0, c->Ua, c->Ub, c->V0,
                   c->Va,     c->Vb,         c->kappa,      c->sigma, c->Fhat, c->t, c->t_end,
-                  c->dt,     c->smax,       c->status, c->bad};
+                  c->dt,     c->smax,       c->status, c->bad,   c->jc};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;
@@ -333,6 +335,7 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
   A(dalloc(c, &c->smax, n_inst));
   A(dalloc(c, &c->status, n_inst));
   A(dalloc(c, &c->bad, (size_t)c->ncells));
+  A(dalloc(c, &c->jc, (size_t)17 * c->ncells));
   if (s == RRMHD_OK) {
     cudaStream_t st = c->stream;
     A(cuda_check(c, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * n_inst,
@@ -356,6 +359,7 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
     A(cuda_check(c, cudaMemsetAsync(c->U0, 0, sizeof(double) * N12, st), "memset"));
     A(cuda_check(c, cudaMemsetAsync(c->V0, 0, sizeof(double) * N12, st), "memset"));
     A(cuda_check(c, cudaMemsetAsync(c->bad, 0, (size_t)c->ncells, st), "memset"));
+    A(cuda_check(c, cudaMemsetAsync(c->jc, 0, sizeof(double) * 17 * c->ncells, st), "memset"));
     A(cuda_check(c, cudaStreamSynchronize(st), "sync"));  // host vectors go out of scope
   }
   if (s == RRMHD_OK) {
@@ -420,6 +424,8 @@ static rrmhd_status refresh_state(rrmhd_ctx* c) {
   RR_CUDA(c, cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long) * c->n_inst, c->stream));
   RR_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(int) * c->n_inst, c->stream));
   RR_CUDA(c, cudaMemsetAsync(c->dt, 0, sizeof(double) * c->n_inst, c->stream));
+  // a new state starts with an empty Jacobian cache (validity plane)
+  RR_CUDA(c, cudaMemsetAsync(c->jc + (size_t)16 * c->ncells, 0, sizeof(double) * c->ncells, c->stream));
   rr::launch_signal_f64(c->P, b, cur_V(c), c->stream);
   RR_CUDA(c, cudaGetLastError());
   return RRMHD_OK;

@@ -118,7 +118,13 @@ __device__ __forceinline__ int cell_update_f32(const StageArgs& a, int64_t c, co
   }
   double vs[NV];
   load12(a.Vs, N, c, vs);
-  return implicit_cell(a.P, a.kappa[c], a.sigma[c], cw * dt, Ust, prim_Z(a.P, vs), Un, Vn);
+  double jc[17];
+#pragma unroll
+  for (int k = 0; k < 17; ++k) jc[k] = a.jc[k * N + c];
+  const int rc = implicit_cell(a.P, a.kappa[c], a.sigma[c], cw * dt, Ust, prim_Z(a.P, vs), Un, Vn, jc);
+#pragma unroll
+  for (int k = 0; k < 17; ++k) a.jc[k * N + c] = jc[k];
+  return rc;
 }
 
 __device__ __forceinline__ void store_cell(const StageArgs& a, int64_t c, const double* Un,

@@ -279,11 +279,18 @@ __device__ __forceinline__ void picard_matrix(const ImpCell& c, const double* X,
 // less than 2x or no descent is found; Armijo backtracking on |R|^2; converged
 // when the full step is <= imp_tol * E_r.  Returns true on convergence.
 static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c, double* X, double* R,
-                                        double* V, double* Z) {
+                                        double* V, double* Z, const double* Min, double* Mout) {
   double J[4][4];
   int need_fd = 0, fresh_fd = 0, first = 1;
   double prev = -1.0;
-  picard_matrix(c, X, V, J);
+  if (Min) {  // the cell's matrix from its previous solve: J = I + h M
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) J[i][j] = (i == j ? 1.0 : 0.0) + c.hdt * Min[4 * i + j];
+  } else {
+    picard_matrix(c, X, V, J);
+  }
   for (int m = 1; m <= P.imp_maxit; ++m) {
     if (need_fd) {
       const double h = 1e-7 * X[0];
@@ -334,6 +341,10 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
 #pragma unroll
       for (int k = 0; k < NV; ++k) V[k] = Vn[k];
       *Z = Zn;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Mout[4 * i + j] = (J[i][j] - (i == j ? 1.0 : 0.0)) / c.hdt;
       return true;
     }
     const double r0 = ((R[0] * R[0] + R[1] * R[1]) + R[2] * R[2]) + R[3] * R[3];
@@ -397,9 +408,12 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
 constexpr int IMP_LADDER = 6;  // continuation fallback starts at h / 2^6
 
 // Implicit step of one cell (Sec. 3.3).  Writes U and V on success; returns a Status.
+// jc (may be null): the cell's Jacobian cache, M = (J - I)/h of its last converged
+// solve (16 entries) and a validity flag jc[16]; a valid entry replaces C^(m) as the
+// first matrix, and the converged matrix is stored back (cleared on failure).
 __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, double sigma,
                                              double hdt, const double* Us, double Zguess,
-                                             double* U, double* V) {
+                                             double* U, double* V, double* jc = nullptr) {
   if ((kappa == 0.0 && sigma == 0.0) || hdt == 0.0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) U[k] = Us[k];
@@ -422,7 +436,8 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
   double R[4], Z = Zguess;
   // no admissible matter state at X*: the explicit update U* itself is inadmissible
   if (!imp_residual(P, c, X, Zguess, R, V, &Z)) return ST_C2P;
-  bool ok = imp_newton(P, c, X, R, V, &Z);
+  double Mnew[16];
+  bool ok = imp_newton(P, c, X, R, V, &Z, (jc && jc[16] != 0.0) ? jc : nullptr, Mnew);
   if (!ok) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) X[i] = c.Xs[i];
@@ -431,8 +446,13 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
     for (int j = IMP_LADDER; j >= 0 && ok; --j) {
       c.hdt = hdt / (double)(1 << j);
       ok = imp_residual(P, c, X, Z, R, V, &Z);
-      if (ok) ok = imp_newton(P, c, X, R, V, &Z);
+      if (ok) ok = imp_newton(P, c, X, R, V, &Z, nullptr, Mnew);
     }
+  }
+  if (jc) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) jc[k] = ok ? Mnew[k] : 0.0;
+    jc[16] = ok ? 1.0 : 0.0;
   }
   if (!ok) return ST_IMPLICIT;
   matter_state(c, X, U);
