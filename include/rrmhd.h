@@ -46,7 +46,8 @@ typedef enum {
     RRMHD_EINVAL = 10,    /* invalid argument                                   */
     RRMHD_ENOMEM = 11,    /* device allocation failed                           */
     RRMHD_ECUDA = 12,     /* CUDA runtime error                                 */
-    RRMHD_ECAPACITY = 13  /* input larger than an alloc-free entry point's fixed scratch */
+    RRMHD_ECAPACITY = 13, /* input larger than a fixed capacity (alloc-free scratch, server budget) */
+    RRMHD_ETIMEOUT = 14   /* a server still had work when the wait ran out           */
 } rrmhd_status;
 
 enum { RRMHD_RECON_GODUNOV = 0, RRMHD_RECON_MINMOD = 1, RRMHD_RECON_MC = 2, RRMHD_RECON_VANLEER = 3 };
@@ -212,6 +213,98 @@ rrmhd_status rrmhd_prim_z(rrmhd_ctx* ctx, const double* V, double* Z, int64_t n)
 #define RRMHD_NOALLOC_MAX_CELLS 33554432
 rrmhd_status rrmhd_cfl_dt_noalloc(const rrmhd_grid* grid, const rrmhd_opts* opts, const double* V,
                                   double* dt, void* cuda_stream);
+
+/* ---- Serving loop (no counterpart in the paper) ------------------------------
+ * A server accepts solve requests -- one 1D, 2D or 3D grid with its primitive state,
+ * opacities and end time each -- at any moment, from any host thread, and runs them
+ * to completion on the current device with continuous batching.
+ *  - Every request in the resident set is advanced by one IMEX-RK3 step per server
+ *    step, with its own time step and end time, exactly as in a context: its result
+ *    does not depend on which other requests share the device with it.
+ *  - Between steps, finished requests (t = t_end, or a failure) leave.  Their
+ *    primitives are copied to the caller's buffer.  Waiting requests are admitted in
+ *    arrival order while they fit the resident bounds (cells, faces and slots, from
+ *    the memory budget).  The resident state is then repacked into one contiguous
+ *    batch: one gather kernel, no host round trip.
+ *  - One host thread per server (the engine) does all device work, on its own
+ *    streams, split into `opts.lanes` concurrent sub-batches.
+ * Times are seconds of the host's steady clock since rrmhd_server_create. */
+typedef struct rrmhd_server rrmhd_server;
+
+typedef struct {
+    int64_t mem_bytes;           /* device memory for resident state; 0: half the free memory */
+    int64_t max_resident_cells;  /* admission bound on the cells stepped together (it bounds
+                                    the step time); 0: what mem_bytes holds              */
+    int     max_resident;        /* admission bound on resident requests (slots); 0: 4096 */
+} rrmhd_server_config;
+
+typedef struct {
+    int64_t id;          /* as returned by rrmhd_server_submit                          */
+    int32_t status;      /* RRMHD_OK, or the instance's failure (then the output is its
+                            last good state)                                          */
+    int32_t steps;       /* IMEX steps taken                                            */
+    int64_t cells;       /* cells of the request's grid                                 */
+    double  t;           /* time reached (= t_end when status is RRMHD_OK)              */
+    double  submit_s;    /* arrival                                                     */
+    double  admit_s;     /* entry into the resident set                                 */
+    double  done_s;      /* output written; time to solution = done_s - submit_s        */
+} rrmhd_result;
+
+typedef struct {
+    int64_t submitted, admitted, completed, failed;
+    int64_t steps;                 /* server steps (one IMEX step of every resident request) */
+    int64_t zone_updates;          /* cells x steps of the resident requests that advanced    */
+    int64_t relayouts;             /* times the resident set changed                         */
+    int64_t resident, resident_cells, peak_resident_cells, pending;
+    int64_t cap_cells, cap_faces;  /* resident bounds derived from the configuration         */
+    double  busy_s;                /* host wall time spent inside server steps               */
+} rrmhd_server_stats;
+
+/* Creates a server on the current device and starts its engine thread.
+ * opts: host, shared by every request (gamma, precision, lanes, ...); cfg: host or
+ * NULL for the defaults.  Device memory for the resident bounds is allocated here,
+ * once: about 1.1 KB per resident cell.  Returns EINVAL for bad options, ENOMEM if
+ * the allocation fails. */
+rrmhd_status rrmhd_server_create(const rrmhd_opts* opts, const rrmhd_server_config* cfg,
+                                 rrmhd_server** out);
+
+/* Queues one request.  grid: host; V: host double[12][ncells] primitives, kappa,
+ * sigma: host double[ncells] (copied before the call returns); t_end: end time
+ * (the request starts at t = 0).  V_out: host double[12][ncells] that receives the
+ * final primitives.  It is owned by the caller and must stay valid until
+ * rrmhd_server_poll has returned the request's result.  id: host, receives the
+ * request's id.  Thread-safe.  Returns EINVAL for a bad grid or NULL buffers,
+ * ECAPACITY for a grid larger than the resident bounds (it could never be
+ * admitted), ECUDA once the engine has failed. */
+rrmhd_status rrmhd_server_submit(rrmhd_server* srv, const rrmhd_grid* grid, const double* V,
+                                 const double* kappa, const double* sigma, double t_end,
+                                 double* V_out, int64_t* id);
+
+/* Moves up to max results of completed requests into out (host), in completion
+ * order; returns how many.  Thread-safe. */
+int rrmhd_server_poll(rrmhd_server* srv, rrmhd_result* out, int max);
+
+/* Blocks until no request is waiting or resident, or until timeout_s seconds have
+ * passed (RRMHD_ETIMEOUT).  Returns ECUDA if the engine failed. */
+rrmhd_status rrmhd_server_wait_idle(rrmhd_server* srv, double timeout_s);
+
+/* Counters of the server so far (host). */
+rrmhd_status rrmhd_server_get_stats(rrmhd_server* srv, rrmhd_server_stats* st);
+
+/* The admission rule on its own (host only, no device work): given the cells and
+ * faces of the waiting requests in arrival order (host arrays of n_waiting), the
+ * free cells, faces and slots of the resident set, returns how many requests
+ * from the head of the queue are admitted.  Arrival order is kept: a request that
+ * does not fit blocks the ones behind it. */
+int rrmhd_server_admission(const int64_t* cells, const int64_t* faces, int n_waiting,
+                           int64_t free_cells, int64_t free_faces, int free_slots);
+
+/* Text of the server's last error (static storage owned by srv). */
+const char* rrmhd_server_last_error(rrmhd_server* srv);
+
+/* Stops the engine thread (after its current step), drops waiting requests and
+ * releases the device memory. */
+void rrmhd_server_destroy(rrmhd_server* srv);
 
 /* Text of the last error of this context (static storage owned by ctx). */
 const char* rrmhd_last_error(const rrmhd_ctx* ctx);

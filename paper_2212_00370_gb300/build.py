@@ -25,8 +25,10 @@ UNITS = {
     "rrmhd_api.cu": [],
     "rrmhd_noalloc.cu": ["--fmad=false"],
     "rrmhd_f32.cu": [],
+    "rrmhd_server.cu": ["--fmad=false"],
 }
-HEADERS = ["physics_f64.cuh", "scheme_f64.cuh", "physics_f32.cuh", "batch.h", "batch_index.cuh"]
+HEADERS = ["physics_f64.cuh", "scheme_f64.cuh", "physics_f32.cuh", "batch.h", "batch_index.cuh",
+           "engine.h"]
 
 
 def _deps():

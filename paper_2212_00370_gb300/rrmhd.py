@@ -20,7 +20,7 @@ RECON = {"godunov": 0, "minmod": 1, "mc": 2, "vanleer": 3}
 BC = {"outflow": 0, "periodic": 1}
 PRECISION = {"fp64": 0, "fp32_bulk": 1}
 STATUS = {0: "OK", 1: "EC2P", 2: "EIMPLICIT", 3: "EUNPHYS", 10: "EINVAL", 11: "ENOMEM", 12: "ECUDA",
-          13: "ECAPACITY"}
+          13: "ECAPACITY", 14: "ETIMEOUT"}
 
 
 class rrmhd_grid(C.Structure):
@@ -32,6 +32,23 @@ class rrmhd_opts(C.Structure):
                 ("pvm_eps", C.c_double), ("recon", C.c_int), ("beta_mode", C.c_int),
                 ("precision", C.c_int), ("c2p_maxit", C.c_int), ("imp_maxit", C.c_int),
                 ("imp_tol", C.c_double), ("lanes", C.c_int)]
+
+
+class rrmhd_server_config(C.Structure):
+    _fields_ = [("mem_bytes", C.c_int64), ("max_resident_cells", C.c_int64), ("max_resident", C.c_int)]
+
+
+class rrmhd_result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("steps", C.c_int32), ("cells", C.c_int64),
+                ("t", C.c_double), ("submit_s", C.c_double), ("admit_s", C.c_double),
+                ("done_s", C.c_double)]
+
+
+class rrmhd_server_stats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in (
+        "submitted", "admitted", "completed", "failed", "steps", "zone_updates", "relayouts",
+        "resident", "resident_cells", "peak_resident_cells", "pending", "cap_cells", "cap_faces")] + [
+        ("busy_s", C.c_double)]
 
 
 class RRMHDError(RuntimeError):
@@ -70,6 +87,17 @@ _SIGNATURES = [
     ("rrmhd_profile_step", C.c_int, [_VP, _DP]),
     ("rrmhd_launches_per_step", C.c_int, [_VP]),
     ("rrmhd_cfl_dt_noalloc", C.c_int, [C.POINTER(rrmhd_grid), C.POINTER(rrmhd_opts), _VP, _VP, _VP]),
+    ("rrmhd_server_create", C.c_int, [C.POINTER(rrmhd_opts), C.POINTER(rrmhd_server_config),
+                                      C.POINTER(_VP)]),
+    ("rrmhd_server_submit", C.c_int, [_VP, C.POINTER(rrmhd_grid), _VP, _VP, _VP, C.c_double, _VP,
+                                      C.POINTER(C.c_int64)]),
+    ("rrmhd_server_poll", C.c_int, [_VP, C.POINTER(rrmhd_result), C.c_int]),
+    ("rrmhd_server_wait_idle", C.c_int, [_VP, C.c_double]),
+    ("rrmhd_server_get_stats", C.c_int, [_VP, C.POINTER(rrmhd_server_stats)]),
+    ("rrmhd_server_admission", C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int,
+                                         C.c_int64, C.c_int64, C.c_int]),
+    ("rrmhd_server_last_error", C.c_char_p, [_VP]),
+    ("rrmhd_server_destroy", None, [_VP]),
     ("rrmhd_last_error", C.c_char_p, [_VP]),
 ]
 
@@ -266,3 +294,73 @@ class Context:
             self.ctx, float(hdt), _ptr(Ustar.contiguous()),
             _ptr(None if Zguess is None else Zguess.contiguous()), _ptr(U), _ptr(V), _ptr(st)))
         return U, V, st
+
+
+def server_admission(cells, faces, free_cells, free_faces, free_slots):
+    """The server's admission rule (host only): how many requests from the head of
+    the waiting queue (cells[i], faces[i] in arrival order) are admitted."""
+    c = np.ascontiguousarray(cells, dtype=np.int64)
+    f = np.ascontiguousarray(faces, dtype=np.int64)
+    return lib().rrmhd_server_admission(c.ctypes.data_as(C.POINTER(C.c_int64)),
+                                        f.ctypes.data_as(C.POINTER(C.c_int64)), len(c),
+                                        int(free_cells), int(free_faces), int(free_slots))
+
+
+class Server:
+    """A librrmhd serving loop: requests are submitted from host arrays and run to
+    completion on the current device with continuous batching."""
+
+    def __init__(self, mem_bytes=0, max_resident_cells=0, max_resident=0, **opts):
+        self.opts = make_opts(**opts)
+        cfg = rrmhd_server_config(int(mem_bytes), int(max_resident_cells), int(max_resident))
+        self.srv = C.c_void_p()
+        rc = lib().rrmhd_server_create(C.byref(self.opts), C.byref(cfg), C.byref(self.srv))
+        if rc != 0:
+            raise RRMHDError(rc, "rrmhd_server_create")
+        self._out = {}  # id -> output array, alive until its result is polled
+
+    def _check(self, rc):
+        if rc != 0:
+            raise RRMHDError(rc, lib().rrmhd_server_last_error(self.srv).decode())
+
+    def submit(self, grid, V, kappa, sigma, t_end):
+        """grid: rrmhd_grid; V: (12, n) float64; kappa, sigma: (n,) float64.  Returns the id."""
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        out = np.empty_like(V)
+        rid = C.c_int64()
+        self._check(lib().rrmhd_server_submit(
+            self.srv, C.byref(grid), C.c_void_p(V.ctypes.data), C.c_void_p(kappa.ctypes.data),
+            C.c_void_p(sigma.ctypes.data), float(t_end), C.c_void_p(out.ctypes.data), C.byref(rid)))
+        self._out[rid.value] = out
+        return rid.value
+
+    def poll(self, max_results=4096):
+        """Completed requests since the last poll: list of (result dict, final V)."""
+        buf = (rrmhd_result * max_results)()
+        k = lib().rrmhd_server_poll(self.srv, buf, max_results)
+        out = []
+        for r in buf[:k]:
+            d = {f: getattr(r, f) for f, _ in rrmhd_result._fields_}
+            out.append((d, self._out.pop(r.id)))
+        return out
+
+    def wait_idle(self, timeout_s=60.0):
+        self._check(lib().rrmhd_server_wait_idle(self.srv, float(timeout_s)))
+
+    def stats(self):
+        st = rrmhd_server_stats()
+        self._check(lib().rrmhd_server_get_stats(self.srv, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in rrmhd_server_stats._fields_}
+
+    def close(self):
+        if self.srv:
+            lib().rrmhd_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

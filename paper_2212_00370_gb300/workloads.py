@@ -12,6 +12,8 @@ configurations:
       log-uniform rho, p, E_r, kappa, sigma; W ~ U[1,10]; |F_r|/E_r ~ U[0,0.99].
   C2  2D 1024^2 periodic magnetised blast with smooth velocity and log-normal kappa.
   C3  3D 256^3 periodic turbulent box.
+  C4  serving mix: Poisson arrivals of 1D (70 %, N ~ U{256..4096}) and planar 2D
+      (30 %, side ~ U{128..512}) Riemann problems with C1 states, t_end 0.2.
 Seeds: 2212003700 + configuration index unless given.
 """
 import dataclasses
@@ -186,3 +188,38 @@ def turbulent_3d(n=256, seed=SEED_BASE + 3):
     g = {"ndim": 3, "n": (n, n, n), "dx": (h, h, h), "bc": ("periodic",) * 3}
     return Workload("C3-turbulent-3d-%d" % n, [g], V, kappa, 0.1 * kappa, np.array([np.inf]),
                     4.0 / 3.0, 1.0, 0.4)
+
+
+def serving_requests(n_req, rate=200.0, seed=SEED_BASE + 4, frac_1d=0.7, n1d=(256, 4096),
+                     side2d=(128, 512), t_end=0.2):
+    """C4 arrival process: n_req requests with exponential inter-arrival times of
+    mean 1/rate seconds; each is 1D with probability frac_1d (N ~ U{n1d}) or a
+    planar 2D problem (side ~ U{side2d}).  Returns light specs (arrival time, kind,
+    size, per-request seed); ``serving_request`` draws the arrays of one spec."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    specs = []
+    for k in range(n_req):
+        one_d = rng.uniform() < frac_1d
+        size = int(rng.integers(n1d[0], n1d[1] + 1)) if one_d else int(rng.integers(side2d[0], side2d[1] + 1))
+        specs.append({"arrival": float(t[k]), "ndim": 1 if one_d else 2, "size": size,
+                      "seed": int(rng.integers(2 ** 62)), "t_end": float(t_end)})
+    return specs
+
+
+def serving_request(spec):
+    """Arrays of one C4 request: a Riemann problem split at x = 0.5 with the two
+    states drawn as in C1 (normal field B_x shared), outflow on every side; 2D
+    requests are planar (uniform in y).  Returns (grid dict, V, kappa, sigma, t_end)."""
+    rng = np.random.default_rng(spec["seed"])
+    n = spec["size"]
+    Bx = rng.uniform(-1, 1)
+    (VL, kL, sL), (VR, kR, sR) = _side_state(rng, Bx), _side_state(rng, Bx)
+    left = (np.arange(n) + 0.5) / n < 0.5
+    if spec["ndim"] == 2:
+        left = np.tile(left, n)   # x fastest, n rows
+        g = {"ndim": 2, "n": (n, n, 1), "dx": (1.0 / n, 1.0 / n, 1.0), "bc": ("outflow",) * 3}
+    else:
+        g = grid1d(n)
+    V = np.ascontiguousarray(np.where(left[None, :], VL[:, None], VR[:, None]))
+    return g, V, np.where(left, kL, kR), np.where(left, sL, sR), spec["t_end"]

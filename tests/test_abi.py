@@ -45,3 +45,31 @@ def test_default_opts_without_gpu(lib_path):
     o = rrmhd.make_opts()
     assert o.gamma == pytest.approx(5 / 3) and o.pvm_eps == 1e-8 and o.recon == 3
     assert o.beta_mode == 1 and o.cfl == pytest.approx(0.4)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """ctypes mirrors of the header's structs have the C sizes and field offsets."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"rrmhd_grid": rrmhd.rrmhd_grid, "rrmhd_opts": rrmhd.rrmhd_opts,
+               "rrmhd_server_config": rrmhd.rrmhd_server_config,
+               "rrmhd_result": rrmhd.rrmhd_result, "rrmhd_server_stats": rrmhd.rrmhd_server_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rrmhd.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[name + "." + f]) == getattr(cls, f).offset, (name, f)

@@ -1,0 +1,177 @@
+"""Serving loop (continuous batching) on the GPU.
+
+Every request's result must be the same alone and in a mix whose membership
+changes while it runs (requests arriving and leaving, repacks of the resident
+batch).  The per-instance arithmetic does not depend on the batch: results are
+compared bit for bit, in both precisions, against the request run alone and
+against the context path, and (FP64, small cases) against the oracle.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from gpu_helpers import compare_bitwise, oracle_grid, oracle_params
+from paper_2212_00370_gb300 import rrmhd
+from paper_2212_00370_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GAMMA = 4.0 / 3.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_00370_gb300 import build
+    build.build()
+
+
+def small_requests(n, seed, t_end=0.04):
+    """A mix of small 1D (16..300 cells) and planar 2D (8^2..24^2) requests with C1 states."""
+    specs = W.serving_requests(n, rate=1e6, seed=seed, frac_1d=0.6, n1d=(16, 300), side2d=(8, 24),
+                               t_end=t_end)
+    return [W.serving_request(s) for s in specs]
+
+
+def grid_of(g):
+    return rrmhd.make_grid(g["ndim"], g["n"], g["dx"], g["bc"])
+
+
+def run_alone(req, precision, lanes=1):
+    srv = rrmhd.Server(gamma=GAMMA, precision=precision, lanes=lanes, mem_bytes=1 << 28)
+    g, V, k, s, te = req
+    srv.submit(grid_of(g), V, k, s, te)
+    srv.wait_idle(120)
+    (res, out), = srv.poll()
+    srv.close()
+    return res, out
+
+
+def run_context(req, precision):
+    g, V, k, s, te = req
+    ctx = rrmhd.Context([grid_of(g)], gamma=GAMMA, precision=precision, lanes=1)
+    ctx.set_opacity(torch.tensor(k, device="cuda"), torch.tensor(s, device="cuda"))
+    ctx.set_state(torch.tensor(V, device="cuda"))
+    ctx.set_times(np.zeros(1), np.array([te]))
+    ctx.imex_step(20000)
+    _, Vg = ctx.get_state()
+    t, _ = ctx.get_times()
+    return Vg.cpu().numpy(), t[0], ctx.inst_status()[0]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_server_matches_context_path(precision):
+    for req in small_requests(4, seed=3):
+        res, out = run_alone(req, precision)
+        Vc, tc, stc = run_context(req, precision)
+        assert res["status"] == stc
+        if stc == 0:
+            assert res["t"] == tc == req[4]
+        compare_bitwise(out, Vc, "server vs context")
+
+
+def test_server_matches_oracle_fp64():
+    import oracle as O
+    req = small_requests(6, seed=5)[4]   # 1D, 194 cells, 15 steps to t_end
+    g, V, k, s, te = req
+    res, out = run_alone(req, "fp64")
+    P = O.Params(gamma=GAMMA, a_rad=1.0, cfl=0.4)
+    Vo = np.ascontiguousarray(V).copy()
+    U = O.prim2con(Vo, P)
+    t, steps, nfail = O.run(oracle_grid(g), 0.0, te, U, Vo, k, s, P, max_steps=20000)
+    assert res["status"] == 0 and nfail == 0
+    assert res["steps"] == steps and res["t"] == t
+    compare_bitwise(out, Vo, "server vs oracle")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_alone_equals_mix(precision):
+    """Requests arrive in three waves while earlier ones run; the resident set is
+    repacked many times; every result equals the same request run alone."""
+    reqs = small_requests(18, seed=7)
+    # a long-running request that stays resident while the others come and go
+    reqs[0] = W.serving_request({"ndim": 1, "size": 400, "seed": 99, "t_end": 0.2, "arrival": 0.0})
+    alone = [run_alone(r, precision) for r in reqs]
+    srv = rrmhd.Server(gamma=GAMMA, precision=precision, lanes=4, mem_bytes=1 << 28)
+    ids = {}
+    for w0, w1, pause in [(0, 6, 0.05), (6, 12, 0.05), (12, 18, 0.0)]:
+        for j in range(w0, w1):
+            g, V, k, s, te = reqs[j]
+            ids[srv.submit(grid_of(g), V, k, s, te)] = j
+        time.sleep(pause)
+    srv.wait_idle(300)
+    got = srv.poll()
+    st = srv.stats()
+    srv.close()
+    assert len(got) == len(reqs) and st["completed"] == len(reqs)
+    assert st["relayouts"] >= 3
+    spans = {}
+    for res, out in got:
+        j = ids[res["id"]]
+        ra, oa = alone[j]
+        assert res["status"] == ra["status"] and res["steps"] == ra["steps"] and res["t"] == ra["t"]
+        compare_bitwise(out, oa, f"request {j} mixed vs alone")
+        spans[j] = (res["admit_s"], res["done_s"])
+    # the long request shared the device with requests of every wave
+    a0, d0 = spans[0]
+    for j in (6, 17):
+        aj, dj = spans[j]
+        assert aj < d0 and a0 < dj
+
+
+def test_admission_by_memory_bound():
+    """A resident bound smaller than the offered work: requests wait, the bound holds,
+    and results still equal the alone runs."""
+    reqs = small_requests(10, seed=11)
+    cells = [int(np.prod(r[0]["n"])) for r in reqs]
+    bound = max(cells) + 64
+    alone = [run_alone(r, "fp64") for r in reqs]
+    srv = rrmhd.Server(gamma=GAMMA, precision="fp64", lanes=2, max_resident_cells=bound,
+                       mem_bytes=1 << 28)
+    ids = {}
+    for j, (g, V, k, s, te) in enumerate(reqs):
+        ids[srv.submit(grid_of(g), V, k, s, te)] = j
+    srv.wait_idle(300)
+    st = srv.stats()
+    got = srv.poll()
+    srv.close()
+    assert st["cap_cells"] == bound and st["peak_resident_cells"] <= bound
+    assert st["peak_resident_cells"] < sum(cells)
+    for res, out in got:
+        j = ids[res["id"]]
+        compare_bitwise(out, alone[j][1], f"request {j} under the bound vs alone")
+
+
+def test_capacity_and_invalid_requests_are_rejected():
+    srv = rrmhd.Server(gamma=GAMMA, max_resident_cells=1000, mem_bytes=1 << 26)
+    V = np.zeros((12, 2000))
+    with pytest.raises(rrmhd.RRMHDError) as e:
+        srv.submit(rrmhd.make_grid(1, (2000,), (1 / 2000,)), V, V[0], V[0], 0.1)
+    assert e.value.code == 13
+    with pytest.raises(rrmhd.RRMHDError) as e:
+        srv.submit(rrmhd.make_grid(1, (0,), (0.1,)), V, V[0], V[0], 0.1)
+    assert e.value.code == 10
+    assert srv.stats()["submitted"] == 0
+    srv.close()
+
+
+def test_failed_request_does_not_disturb_the_others():
+    reqs = small_requests(4, seed=13)
+    g, V, k, s, te = reqs[1]
+    V = V.copy()
+    V[8, 3] = 0.0   # E_r = 0: an inadmissible cell
+    reqs[1] = (g, V, k, s, te)
+    alone = [run_alone(r, "fp64") for r in reqs]
+    assert alone[1][0]["status"] != 0
+    srv = rrmhd.Server(gamma=GAMMA, precision="fp64", lanes=2, mem_bytes=1 << 28)
+    ids = {srv.submit(grid_of(r[0]), *r[1:]): j for j, r in enumerate(reqs)}
+    srv.wait_idle(120)
+    got = srv.poll()
+    srv.close()
+    for res, out in got:
+        j = ids[res["id"]]
+        assert res["status"] == alone[j][0]["status"]
+        compare_bitwise(out, alone[j][1], f"request {j}")
