@@ -57,7 +57,8 @@ def parse():
     p.add_argument("--instances", type=int, default=4096)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-sample", type=int, default=256, help="instances in the CPU sample")
+    p.add_argument("--cpu-sample", type=int, default=4096,
+                   help="instances in the CPU sample (1 step each; default: the whole batch)")
     p.add_argument("--lanes", type=int, default=8, help="independent sub-batches (streams)")
     p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32_bulk"],
                    help="both: FP32-bulk is the headline value, FP64 reported beside it")
@@ -65,6 +66,10 @@ def parse():
                    help="requests of the C4 serving sample (0: skip the serving measurement)")
     p.add_argument("--serve-cells", type=int, default=4_000_000,
                    help="resident-cell bound of the serving loop (bounds its step time)")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default launch shapes instead of autotuning them before timing")
+    p.add_argument("--tuning", default=None,
+                   help='fixed launch shapes as JSON, e.g. \'{"cell_block": 32, "lanes": 32}\' (no autotune)')
     return p.parse_args()
 
 
@@ -189,6 +194,18 @@ def measure(a, precision, rank, world, local):
 
     ctx.imex_step(max(a.warmup, 2))          # warm-up (also builds the step graphs)
     torch.cuda.synchronize()
+    tuning, tune_ms = ctx.get_tuning(), None
+    if a.tuning:
+        ctx.set_tuning(**json.loads(a.tuning))
+        tuning = ctx.get_tuning()
+        ctx.imex_step(1)
+        torch.cuda.synchronize()
+    elif not a.no_autotune:                  # untimed: shapes chosen on this state, state restored
+        t0 = time.perf_counter()
+        tuning, tune_ms = ctx.autotune(repeats=1)
+        tune_s = time.perf_counter() - t0
+        ctx.imex_step(1)                     # warm the chosen shapes' graphs
+        torch.cuda.synchronize()
     st_before = ctx.inst_status()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
     barrier()
@@ -259,12 +276,14 @@ def measure(a, precision, rank, world, local):
            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
            "roofline": roofline, "e2e": e2e, "gpu_launches": ctx.launches_per_step() * a.steps,
            "clocks": clk.summary(), "live": int(live.sum()), "failed": int((~live).sum()),
-           "cells": int(n_cells.sum()), "ncells_state_mb": 12 * 8 * w.ncells / 1e6, "seed": seed}
+           "cells": int(n_cells.sum()), "ncells_state_mb": 12 * 8 * w.ncells / 1e6, "seed": seed,
+           "tuning": tuning, "autotune": None if (a.no_autotune or a.tuning) else
+           {"best_step_ms": tune_ms, "wall_s": round(tune_s, 1), "repeats": 1}}
     ctx.close()
     return out
 
 
-def measure_serving(a):
+def measure_serving(a, tuning=None):
     """C4 serving sample: the first `serve_requests` requests of the C4 arrival process
     (Poisson, 200 requests/s; 70 % 1D N~U{256..4096}, 30 % planar 2D side~U{128..512};
     C1 states; t_end 0.2; FP32-bulk) submitted at their arrival times from a host
@@ -285,7 +304,7 @@ def measure_serving(a):
     offered = sum(zu_max(sp) for sp in all_specs) / all_specs[-1]["arrival"]
 
     srv = rrmhd.Server(gamma=4.0 / 3.0, precision="fp32_bulk", lanes=a.lanes,
-                       max_resident_cells=a.serve_cells)
+                       max_resident_cells=a.serve_cells, tuning=tuning)
     srv.wait_idle(1.0)
 
     def submitter():
@@ -351,7 +370,9 @@ def run_ours(a, rank, world, pool, cores):
                                "precision %s" % (a.instances, precisions[0]),
                    "instances": a.instances, "cells": head["cells"],
                    "live_instances": head["live"], "failed_instances": head["failed"],
-                   "parallelism": "replicas (independent problems per GPU); %d lanes (streams) per GPU" % a.lanes,
+                   "parallelism": "replicas (independent problems per GPU); %d lanes (streams) per GPU"
+                                  % head["tuning"]["lanes"],
+                   "launch_shapes": head["tuning"], "autotune": head["autotune"],
                    "l2": "state %.0f MB per copy > 129 MB L2 (inputs larger than L2)" % head["ncells_state_mb"]},
         "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
         "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
@@ -360,12 +381,13 @@ def run_ours(a, rank, world, pool, cores):
     if len(precisions) > 1:
         f = res["fp64"]
         out["fp64"] = {"value": f["value"], "ms_per_step": f["ms_per_step"], "p50_ms": f["p50_ms"],
+                       "launch_shapes": f["tuning"],
                        "p99_ms": f["p99_ms"], "roofline": f["roofline"], "e2e": f["e2e"],
                        "failed_instances": f["failed"], "clocks": f["clocks"]}
         out["fp32_bulk_speedup_over_fp64"] = head["value"] / f["value"]
         out["gpu_launches"] += f["gpu_launches"]
     if a.serve_requests > 0 and world == 1:
-        out["serving"] = measure_serving(a)
+        out["serving"] = measure_serving(a, res["fp32_bulk"]["tuning"] if "fp32_bulk" in res else None)
     if rank == 0 and pool is not None:
         zps, wall, zc = cpu_oracle(pool, cores, head["seed"], a.instances, a.cpu_sample, 1)
         out["cpu_baseline"] = {"value": zps, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",

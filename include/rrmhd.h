@@ -187,6 +187,41 @@ rrmhd_status rrmhd_profile_step(rrmhd_ctx* ctx, double* ms);
 /* Kernel launches one rrmhd_imex_step step enqueues (for launch accounting). */
 int rrmhd_launches_per_step(const rrmhd_ctx* ctx);
 
+/* ---- Launch shapes and the autotuner (no counterpart in the paper) ----------
+ * How the face and cell kernels spread their work over threads, and into how many
+ * concurrent lanes a context splits its instances.  Shapes never change results:
+ * every face and cell is computed once, by the same arithmetic, whatever the
+ * shape (bit-identical output).
+ *   *_block        threads per block: 32, 64, 128 or 256
+ *   *_per_thread   faces or cells per thread of the grid schedule: 1 or 2
+ *   *_persistent   1: a resident grid (SMs x resident blocks per SM) whose warps take
+ *                  chunks of 32 consecutive items from a counter until none are
+ *                  left (per_thread must be 1); 0: one thread per item(s)
+ *   lanes          >= 1; see rrmhd_opts.lanes
+ * Defaults: 128 threads, 1 item per thread, grid schedule, opts.lanes. */
+typedef struct {
+    int face_block, face_per_thread, face_persistent;
+    int cell_block, cell_per_thread, cell_persistent;
+    int lanes;
+} rrmhd_tuning;
+
+/* The context's current shapes (host out). */
+rrmhd_status rrmhd_get_tuning(const rrmhd_ctx* ctx, rrmhd_tuning* t);
+
+/* Sets the shapes (host in); EINVAL for a shape that is not compiled.  Synchronises
+ * the context's stream; the next step rebuilds its CUDA graphs. */
+rrmhd_status rrmhd_set_tuning(rrmhd_ctx* ctx, const rrmhd_tuning* t);
+
+/* Chooses the shapes for this context's batch by timing real steps from its
+ * current state: coordinate descent over the cell shapes, then the face shapes,
+ * then the lane count; each candidate is timed over `repeats` steps (CUDA events
+ * on the context's stream, median), each taken from the same saved state.  The
+ * state, times and statuses are restored afterwards, so the context continues as
+ * if no step had been taken; the fastest shapes are kept.  best (host, may be
+ * NULL) receives them, best_ms (host, may be NULL) the median step time.  Allocates
+ * a copy of the state for the duration of the call (ENOMEM if that fails). */
+rrmhd_status rrmhd_autotune(rrmhd_ctx* ctx, int repeats, rrmhd_tuning* best, double* best_ms);
+
 /* rho h W^2 of primitives: V double[12][n] -> Z double[n] (con2prim warm starts). */
 rrmhd_status rrmhd_prim_z(rrmhd_ctx* ctx, const double* V, double* Z, int64_t n);
 
@@ -236,6 +271,7 @@ typedef struct {
     int64_t max_resident_cells;  /* admission bound on the cells stepped together (it bounds
                                     the step time); 0: what mem_bytes holds              */
     int     max_resident;        /* admission bound on resident requests (slots); 0: 4096 */
+    rrmhd_tuning tuning;         /* launch shapes and lanes; all zero: the defaults       */
 } rrmhd_server_config;
 
 typedef struct {

@@ -69,20 +69,38 @@ struct StageArgs {
   int32_t* cell_status;    // optional per-cell status
   uint8_t* bad;            // [ncells] cells whose U* is inadmissible (admissibility fallback)
   double* jc;              // [17][ncells] per-cell Jacobian cache of the implicit solve
+  unsigned long long* work;  // [2] chunk counters of persistent face / cell launches
 };
 
-// FP64 path (bit-compatible with the oracle's arithmetic order)
-void launch_faces_f64(const StageArgs& a, cudaStream_t s);
-void launch_cells_f64(const StageArgs& a, cudaStream_t s);
+// How a kernel spreads its work items over threads (launch_shape.cuh).
+struct LaunchShape {
+  int block = 128;      // threads per block: 32, 64, 128, 256
+  int per_thread = 1;   // items per thread of the grid schedule: 1, 2
+  int persistent = 0;   // 1: resident grid, warps take 32-item chunks from a counter
+};
+
+struct Tuning {
+  LaunchShape faces, cells;
+};
+
+// FP64 path (bit-compatible with the oracle's arithmetic order).  A persistent
+// shape needs a.work zeroed on the stream before the launch (the launchers do it).
+void launch_faces_f64(const StageArgs& a, const LaunchShape& sh, cudaStream_t s);
+void launch_cells_f64(const StageArgs& a, const LaunchShape& sh, cudaStream_t s);
 void launch_fallback_f64(const StageArgs& a, cudaStream_t s);
 void launch_signal_f64(const Params& P, const Batch& b, const double* V, cudaStream_t s);
 
 // FP32-bulk form: FP32 faces (tangent PVM products), FP64 cells
-void launch_faces_f32(const StageArgs& a, cudaStream_t s);
-void launch_cells_f32(const StageArgs& a, cudaStream_t s);
+void launch_faces_f32(const StageArgs& a, const LaunchShape& sh, cudaStream_t s);
+void launch_cells_f32(const StageArgs& a, const LaunchShape& sh, cudaStream_t s);
 void launch_fallback_f32(const StageArgs& a, cudaStream_t s);
 void launch_widen_f32(const float* F32, int64_t fstride32, int64_t f_begin, int64_t n, double* F,
                       cudaStream_t s);
+// Resolves the resident-grid sizes of the persistent kernels (occupancy queries);
+// call once per device before any stream capture.  Returns false on a CUDA error.
+bool prepare_launch_shapes();
+bool prepare_launch_shapes_f64();
+bool prepare_launch_shapes_f32();
 void launch_begin_step(const Params& P, const Batch& b, cudaStream_t s);
 void launch_end_step(const Batch& b, cudaStream_t s);
 void launch_prim2con_f64(const Params& P, const double* V, double* U, int64_t n, cudaStream_t s);

@@ -13,6 +13,7 @@
 
 #include "../../include/rrmhd.h"
 #include "batch.h"
+#include "launch_shape.cuh"
 
 namespace rr {
 
@@ -191,7 +192,8 @@ inline Batch make_batch(const Layout& L, const DeviceBufs& B, int i0, int i1) {
 
 inline StageArgs stage_args(const Params& P, const DeviceBufs& B, const Batch& b, int stage,
                             const double* U0, const double* V0, const double* Us,
-                            const double* Vs, double* Uout, double* Vout) {
+                            const double* Vs, double* Uout, double* Vout,
+                            unsigned long long* work = nullptr) {
   StageArgs a;
   a.P = P;
   a.b = b;
@@ -212,20 +214,43 @@ inline StageArgs stage_args(const Params& P, const DeviceBufs& B, const Batch& b
   a.cell_status = nullptr;
   a.bad = B.bad;
   a.jc = B.jc;
+  a.work = work;
   return a;
 }
 
-// The three launch groups of one stage in the given precision.
-inline void launch_stage(int precision, const StageArgs& a, cudaStream_t s) {
-  if (precision == RRMHD_FP32_BULK) {
-    launch_faces_f32(a, s);
-    launch_cells_f32(a, s);
+inline void launch_faces(int precision, const StageArgs& a, const LaunchShape& sh, cudaStream_t s) {
+  if (precision == RRMHD_FP32_BULK)
+    launch_faces_f32(a, sh, s);
+  else
+    launch_faces_f64(a, sh, s);
+}
+
+inline void launch_cells(int precision, const StageArgs& a, const LaunchShape& sh, cudaStream_t s) {
+  if (precision == RRMHD_FP32_BULK)
+    launch_cells_f32(a, sh, s);
+  else
+    launch_cells_f64(a, sh, s);
+}
+
+inline void launch_fallback(int precision, const StageArgs& a, cudaStream_t s) {
+  if (precision == RRMHD_FP32_BULK)
     launch_fallback_f32(a, s);
-  } else {
-    launch_faces_f64(a, s);
-    launch_cells_f64(a, s);
+  else
     launch_fallback_f64(a, s);
-  }
+}
+
+// The three launch groups of one stage in the given precision and shapes.
+inline void launch_stage(int precision, const Tuning& tu, const StageArgs& a, cudaStream_t s) {
+  launch_faces(precision, a, tu.faces, s);
+  launch_cells(precision, a, tu.cells, s);
+  launch_fallback(precision, a, s);
+}
+
+inline Tuning default_tuning() { return Tuning{}; }
+
+inline bool tuning_ok(const Tuning& t) {
+  return shape_ok(t.faces.block, t.faces.per_thread, t.faces.persistent) &&
+         shape_ok(t.cells.block, t.cells.per_thread, t.cells.persistent);
 }
 
 // One IMEX-RK3 step of the instances of b, from the state in buffer set
@@ -233,20 +258,25 @@ inline void launch_stage(int precision, const StageArgs& a, cudaStream_t s) {
 // stage 1 A -> B, stage 2 (B; A) -> C, stage 3 (C; A) -> B.  No stage writes its
 // inputs, so the admissibility fallback can re-read them.  Launches: begin,
 // 3 x {faces, cells, fallback faces, fallback cells}, end.
-inline void enqueue_step(const Params& P, int precision, const DeviceBufs& B, const Batch& b,
-                         int cur, cudaStream_t s) {
+// work: this stream's two chunk counters (persistent shapes).
+inline void enqueue_step(const Params& P, int precision, const Tuning& tu, const DeviceBufs& B,
+                         const Batch& b, int cur, unsigned long long* work, cudaStream_t s) {
   double* AU = cur ? B.Ua : B.U0;
   double* AV = cur ? B.Va : B.V0;
   double* BU = cur ? B.U0 : B.Ua;
   double* BV = cur ? B.V0 : B.Va;
   launch_begin_step(P, b, s);
-  const StageArgs s1 = stage_args(P, B, b, 1, AU, AV, AU, AV, BU, BV);
-  const StageArgs s2 = stage_args(P, B, b, 2, AU, AV, BU, BV, B.Ub, B.Vb);
-  const StageArgs s3 = stage_args(P, B, b, 3, AU, AV, B.Ub, B.Vb, BU, BV);
-  for (const StageArgs* a : {&s1, &s2, &s3}) launch_stage(precision, *a, s);
+  const StageArgs s1 = stage_args(P, B, b, 1, AU, AV, AU, AV, BU, BV, work);
+  const StageArgs s2 = stage_args(P, B, b, 2, AU, AV, BU, BV, B.Ub, B.Vb, work);
+  const StageArgs s3 = stage_args(P, B, b, 3, AU, AV, B.Ub, B.Vb, BU, BV, work);
+  for (const StageArgs* a : {&s1, &s2, &s3}) launch_stage(precision, tu, *a, s);
   launch_end_step(b, s);
 }
 
-constexpr int kLaunchesPerStep = 2 + 3 * 4;
+// Kernel launches (and counter memsets, which are graph nodes too) of one step.
+inline int launches_per_step(const Tuning& tu) {
+  return 2 + 3 * (4 + (tu.faces.persistent ? 1 : 0) + (tu.cells.persistent ? 1 : 0));
+}
+
 
 }  // namespace rr

@@ -119,11 +119,18 @@ __device__ __forceinline__ void flux(const P32& P, int d, const T* V, const T* U
   const T E = V[8];
   const T F2 = V[9] * V[9] + V[10] * V[10] + V[11] * V[11];
   T f2 = F2 / (E * E);
-  if (val(f2) > 1.f) f2 = cst<T>(1.f);
-  const T xi = (3.f + 4.f * f2) / (5.f + 2.f * tsqrt(4.f - 3.f * f2));
+  const bool clamped = val(f2) > 1.f;
+  if (clamped) f2 = cst<T>(1.f);
+  const T s = tsqrt(4.f - 3.f * f2);
+  const T xi = (3.f + 4.f * f2) / (5.f + 2.f * s);
   const T am = (0.5f * (1.f - xi)) * E;
-  T cm = cst<T>(0.f);
-  if (val(F2) > 0.f) cm = ((0.5f * (3.f * xi - 1.f)) * E) / F2;
+  // P^ij = am delta_ij + cm F_i F_j with cm = E (3 xi - 1) / (2 F^2).  Since
+  // 3 xi - 1 = 6 f^2 / (2 + s) exactly (s^2 = 4 - 3 f^2), cm = 3 / (E (2 + s)): no
+  // cancellation of 3 xi - 1 near f = 0 and no 1/|F|^2.  In FP32 the literal form
+  // leaves ~1e-7 of rounding in 3 xi - 1; divided by F^2 << E^2 that puts a
+  // spurious eigenvalue far above the speed of light into the tangent Jacobian,
+  // outside the range where the PVM polynomial approximates |x|.
+  const T cm = clamped ? (3.f * E) / ((2.f + s) * F2) : 3.f / (E * (2.f + s));
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     const T t = cm * (V[9 + d] * V[9 + j]);

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <limits>
@@ -21,6 +22,7 @@ using rr::StageArgs;
 
 struct Lane {
   Batch b;                      // the lane's instance / cell / face ranges
+  unsigned long long* work = nullptr;  // the lane's chunk counters (persistent shapes)
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per value of rrmhd_ctx::cur
@@ -34,6 +36,8 @@ struct rrmhd_ctx {
   rr::Layout L;                       // packed layout of the instances
   rr::DeviceBufs B;                   // device state and tables
   int cur = 0;                        // the state lives in (U0,V0) when 0, in (Ua,Va) when 1
+  rr::Tuning tune;                    // launch shapes
+  unsigned long long* work = nullptr; // chunk counters: 2 per lane, then 2 for whole-batch calls
   std::vector<Lane> lanes;
   cudaEvent_t fork = nullptr;
   std::string err;
@@ -76,7 +80,52 @@ rrmhd_status dalloc(rrmhd_ctx* c, T** p, size_t count) {
   return cuda_check(c, cudaMalloc((void**)p, count * sizeof(T)), "cudaMalloc");
 }
 
+void destroy_lanes(rrmhd_ctx* c) {
+  for (Lane& L : c->lanes) {
+    if (L.stream) cudaStreamSynchronize(L.stream);
+    for (cudaGraphExec_t g : L.graph)
+      if (g) cudaGraphExecDestroy(g);
+    if (L.done) cudaEventDestroy(L.done);
+    if (L.stream) cudaStreamDestroy(L.stream);
+  }
+  c->lanes.clear();
+  if (c->work) cudaFree(c->work);
+  c->work = nullptr;
+}
+
+// Splits the instances into n lanes of about equal cell count, each with its own
+// stream, completion event and chunk counters.
+rrmhd_status build_lanes(rrmhd_ctx* c, int n) {
+  destroy_lanes(c);
+  const auto ranges = rr::lane_ranges(c->L.cell_off, c->L.n_inst, n);
+  const size_t nw = 2 * (ranges.size() + 1);
+  RR_CUDA(c, cudaMalloc((void**)&c->work, sizeof(unsigned long long) * nw));
+  RR_CUDA(c, cudaMemset(c->work, 0, sizeof(unsigned long long) * nw));
+  for (size_t l = 0; l < ranges.size(); ++l) {
+    Lane lane;
+    lane.b = rr::make_batch(c->L, c->B, ranges[l].first, ranges[l].second);
+    lane.work = c->work + 2 * l;
+    c->lanes.push_back(lane);
+    Lane& L = c->lanes.back();
+    RR_CUDA(c, cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking));
+    RR_CUDA(c, cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
+  }
+  return RRMHD_OK;
+}
+
+// Chunk counters of the whole-batch launches (flux sweep, profiled step).
+unsigned long long* batch_work(const rrmhd_ctx* c) { return c->work + 2 * c->lanes.size(); }
+
 }  // namespace
+
+namespace rr {
+bool prepare_launch_shapes() {
+  static std::once_flag once;
+  static bool ok = false;
+  std::call_once(once, [] { ok = prepare_launch_shapes_f64() && prepare_launch_shapes_f32(); });
+  return ok;
+}
+}  // namespace rr
 
 extern "C" {
 
@@ -99,13 +148,7 @@ void rrmhd_destroy(rrmhd_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  for (Lane& L : c->lanes) {
-    if (L.stream) cudaStreamSynchronize(L.stream);
-    for (cudaGraphExec_t g : L.graph)
-      if (g) cudaGraphExecDestroy(g);
-    if (L.done) cudaEventDestroy(L.done);
-    if (L.stream) cudaStreamDestroy(L.stream);
-  }
+  destroy_lanes(c);
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   const rr::DeviceBufs& B = c->B;
@@ -127,6 +170,7 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
   std::string why;
   for (int i = 0; i < n_inst; ++i)
     if (!rr::grid_ok(grids[i], why)) return RRMHD_EINVAL;
+  if (!rr::prepare_launch_shapes()) return RRMHD_ECUDA;
 
   rrmhd_ctx* c = new rrmhd_ctx();
   c->opts = o;
@@ -182,15 +226,8 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
     A(cuda_check(c, cudaStreamSynchronize(st), "sync"));  // host vectors go out of scope
   }
   if (s == RRMHD_OK) {
-    // lanes: contiguous instance ranges of about equal cell count
-    for (const auto& r : rr::lane_ranges(L.cell_off, n_inst, o.lanes)) {
-      if (s != RRMHD_OK) break;
-      Lane lane;
-      lane.b = rr::make_batch(L, B, r.first, r.second);
-      A(cuda_check(c, cudaStreamCreateWithFlags(&lane.stream, cudaStreamNonBlocking), "stream"));
-      A(cuda_check(c, cudaEventCreateWithFlags(&lane.done, cudaEventDisableTiming), "event"));
-      c->lanes.push_back(lane);
-    }
+    c->tune = rr::default_tuning();
+    A(build_lanes(c, o.lanes));
     A(cuda_check(c, cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming), "event"));
   }
   if (s != RRMHD_OK) {
@@ -295,7 +332,7 @@ static rrmhd_status build_step_graph(rrmhd_ctx* c, Lane& L, int cur) {
   if (!c->cap_stream)
     RR_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   RR_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  rr::enqueue_step(c->P, c->opts.precision, c->B, L.b, cur, c->cap_stream);
+  rr::enqueue_step(c->P, c->opts.precision, c->tune, c->B, L.b, cur, L.work, c->cap_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
   if (e != cudaSuccess) {
@@ -367,16 +404,17 @@ rrmhd_status rrmhd_flux_sweep(rrmhd_ctx* c, int dir, double* Fhat) {
   for (int d = 0; d < 3; ++d) b.f_count[d] = (d == dir) ? b.f_count[d] : 0;
   StageArgs a = stage_args(c, b, 0, cur_U(c), cur_V(c), cur_U(c), cur_V(c), nullptr, nullptr);
   a.check_active = 0;
+  a.work = batch_work(c);
   const int64_t nd = c->L.dir_base[dir + 1] - c->L.dir_base[dir];
   if (c->opts.precision == RRMHD_FP32_BULK) {
     // FP32 fluxes into the context's face buffer, widened into the caller's array
-    rr::launch_faces_f32(a, c->stream);
+    rr::launch_faces_f32(a, c->tune.faces, c->stream);
     rr::launch_widen_f32(a.Fhat32, c->L.nfaces, c->L.dir_base[dir], nd, Fhat, c->stream);
   } else {
     a.Fhat = Fhat;
     a.fstride = nd;
     a.out_base = c->L.dir_base[dir];
-    rr::launch_faces_f64(a, c->stream);
+    rr::launch_faces_f64(a, c->tune.faces, c->stream);
   }
   RR_CUDA(c, cudaGetLastError());
   return RRMHD_OK;
@@ -392,7 +430,7 @@ rrmhd_status rrmhd_implicit_source(rrmhd_ctx* c, double hdt, const double* Ustar
 }
 
 int rrmhd_launches_per_step(const rrmhd_ctx* c) {
-  return c ? (int)c->lanes.size() * rr::kLaunchesPerStep : 0;
+  return c ? (int)c->lanes.size() * (2 + 3 * 4) : 0;
 }
 
 rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
@@ -403,9 +441,10 @@ rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
   double* AV = cur ? c->B.Va : c->B.V0;
   double* BU = cur ? c->B.U0 : c->B.Ua;
   double* BV = cur ? c->B.V0 : c->B.Va;
-  const StageArgs st[3] = {stage_args(c, b, 1, AU, AV, AU, AV, BU, BV),
-                           stage_args(c, b, 2, AU, AV, BU, BV, c->B.Ub, c->B.Vb),
-                           stage_args(c, b, 3, AU, AV, c->B.Ub, c->B.Vb, BU, BV)};
+  unsigned long long* w = batch_work(c);
+  const StageArgs st[3] = {rr::stage_args(c->P, c->B, b, 1, AU, AV, AU, AV, BU, BV, w),
+                           rr::stage_args(c->P, c->B, b, 2, AU, AV, BU, BV, c->B.Ub, c->B.Vb, w),
+                           rr::stage_args(c->P, c->B, b, 3, AU, AV, c->B.Ub, c->B.Vb, BU, BV, w)};
   cudaEvent_t ev[14];
   for (auto& e : ev) RR_CUDA(c, cudaEventCreate(&e));
   cudaStream_t s = c->stream;
@@ -413,13 +452,13 @@ rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
   cudaEventRecord(ev[k++], s);
   rr::launch_begin_step(c->P, b, s);
   cudaEventRecord(ev[k++], s);
-  const bool f32 = c->opts.precision == RRMHD_FP32_BULK;
+  const int pr = c->opts.precision;
   for (int i = 0; i < 3; ++i) {
-    if (f32) rr::launch_faces_f32(st[i], s); else rr::launch_faces_f64(st[i], s);
+    rr::launch_faces(pr, st[i], c->tune.faces, s);
     cudaEventRecord(ev[k++], s);
-    if (f32) rr::launch_cells_f32(st[i], s); else rr::launch_cells_f64(st[i], s);
+    rr::launch_cells(pr, st[i], c->tune.cells, s);
     cudaEventRecord(ev[k++], s);
-    if (f32) rr::launch_fallback_f32(st[i], s); else rr::launch_fallback_f64(st[i], s);
+    rr::launch_fallback(pr, st[i], s);
     cudaEventRecord(ev[k++], s);
   }
   rr::launch_end_step(b, s);
@@ -445,6 +484,156 @@ rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
   }
   for (auto& e : ev) cudaEventDestroy(e);
   return rc;
+}
+
+static rr::Tuning tuning_from(const rrmhd_tuning& t) {
+  rr::Tuning tu;
+  tu.faces = {t.face_block, t.face_per_thread, t.face_persistent};
+  tu.cells = {t.cell_block, t.cell_per_thread, t.cell_persistent};
+  return tu;
+}
+
+static rrmhd_tuning tuning_to(const rr::Tuning& tu, int lanes) {
+  rrmhd_tuning t;
+  t.face_block = tu.faces.block;
+  t.face_per_thread = tu.faces.per_thread;
+  t.face_persistent = tu.faces.persistent;
+  t.cell_block = tu.cells.block;
+  t.cell_per_thread = tu.cells.per_thread;
+  t.cell_persistent = tu.cells.persistent;
+  t.lanes = lanes;
+  return t;
+}
+
+rrmhd_status rrmhd_get_tuning(const rrmhd_ctx* c, rrmhd_tuning* t) {
+  if (!c || !t) return RRMHD_EINVAL;
+  *t = tuning_to(c->tune, c->opts.lanes);
+  return RRMHD_OK;
+}
+
+rrmhd_status rrmhd_set_tuning(rrmhd_ctx* c, const rrmhd_tuning* t) {
+  if (!c || !t) return set_err(c, RRMHD_EINVAL, "null argument");
+  const rr::Tuning tu = tuning_from(*t);
+  if (!rr::tuning_ok(tu) || t->lanes < 1) return set_err(c, RRMHD_EINVAL, "unsupported launch shape");
+  RR_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->tune = tu;
+  c->opts.lanes = t->lanes;
+  return build_lanes(c, t->lanes);  // new lanes, no step graphs yet
+}
+
+rrmhd_status rrmhd_autotune(rrmhd_ctx* c, int repeats, rrmhd_tuning* best, double* best_ms) {
+  if (!c || repeats < 1) return set_err(c, RRMHD_EINVAL, "bad argument");
+  const int n = c->L.n_inst;
+  const size_t N12 = (size_t)12 * c->L.ncells, NJ = (size_t)17 * c->L.ncells;
+  double *sU = nullptr, *sV = nullptr, *sJ = nullptr, *sT = nullptr, *sDt = nullptr;
+  unsigned long long* sM = nullptr;
+  int* sS = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto release = [&] {
+    for (void* p : {(void*)sU, (void*)sV, (void*)sJ, (void*)sT, (void*)sDt, (void*)sM, (void*)sS})
+      if (p) cudaFree(p);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc((void**)&sU, 8 * N12) != cudaSuccess || cudaMalloc((void**)&sV, 8 * N12) != cudaSuccess ||
+      cudaMalloc((void**)&sJ, 8 * NJ) != cudaSuccess || cudaMalloc((void**)&sT, 8 * n) != cudaSuccess ||
+      cudaMalloc((void**)&sDt, 8 * n) != cudaSuccess || cudaMalloc((void**)&sM, 8 * n) != cudaSuccess ||
+      cudaMalloc((void**)&sS, sizeof(int) * n) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return set_err(c, RRMHD_ENOMEM, "autotune: no memory for the saved state");
+  }
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaStream_t st = c->stream;
+  const int cur0 = c->cur;
+  const rr::DeviceBufs& B = c->B;
+  auto copy_state = [&](bool save) -> cudaError_t {
+    double* U = cur0 ? B.Ua : B.U0;
+    double* V = cur0 ? B.Va : B.V0;
+    struct P { void* live; void* saved; size_t bytes; } parts[] = {
+        {U, sU, 8 * N12}, {V, sV, 8 * N12}, {B.jc, sJ, 8 * NJ}, {B.t, sT, 8 * (size_t)n},
+        {B.dt, sDt, 8 * (size_t)n}, {B.smax, sM, 8 * (size_t)n}, {B.status, sS, sizeof(int) * n}};
+    for (const P& q : parts) {
+      cudaError_t e = save ? cudaMemcpyAsync(q.saved, q.live, q.bytes, cudaMemcpyDeviceToDevice, st)
+                           : cudaMemcpyAsync(q.live, q.saved, q.bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
+    if (!save) c->cur = cur0;
+    return cudaSuccess;
+  };
+  rrmhd_status rc = cuda_check(c, copy_state(true), "autotune save");
+  // median step time (ms) of a candidate, each step from the saved state
+  auto trial = [&](const rrmhd_tuning& cand, double& ms) -> rrmhd_status {
+    rrmhd_status r = rrmhd_set_tuning(c, &cand);
+    if (r != RRMHD_OK) return r;
+    RR_CUDA(c, copy_state(false));
+    r = rrmhd_imex_step(c, 1);  // warm: builds the step graphs, loads the kernels
+    if (r != RRMHD_OK) return r;
+    std::vector<float> v;
+    for (int k = 0; k < repeats; ++k) {
+      RR_CUDA(c, copy_state(false));
+      RR_CUDA(c, cudaEventRecord(e0, st));
+      r = rrmhd_imex_step(c, 1);
+      if (r != RRMHD_OK) return r;
+      RR_CUDA(c, cudaEventRecord(e1, st));
+      RR_CUDA(c, cudaEventSynchronize(e1));
+      float x = 0.f;
+      RR_CUDA(c, cudaEventElapsedTime(&x, e0, e1));
+      v.push_back(x);
+    }
+    std::sort(v.begin(), v.end());
+    ms = v[v.size() / 2];
+    return RRMHD_OK;
+  };
+  rrmhd_tuning cur_best = tuning_to(c->tune, c->opts.lanes);
+  double cur_ms = 0.0;
+  if (rc == RRMHD_OK) rc = trial(cur_best, cur_ms);
+  auto consider = [&](const rrmhd_tuning& cand) {
+    if (rc != RRMHD_OK) return;
+    double ms = 0.0;
+    rc = trial(cand, ms);
+    if (rc == RRMHD_OK && ms < cur_ms) {
+      cur_ms = ms;
+      cur_best = cand;
+    }
+  };
+  const int blocks[4] = {32, 64, 128, 256};
+  // 1. cell shapes
+  for (int persistent = 0; persistent <= 1; ++persistent)
+    for (int bsz : blocks)
+      for (int pt = 1; pt <= (persistent ? 1 : 2); ++pt) {
+        rrmhd_tuning t = cur_best;
+        t.cell_block = bsz;
+        t.cell_per_thread = pt;
+        t.cell_persistent = persistent;
+        consider(t);
+      }
+  // 2. face shapes
+  for (int persistent = 0; persistent <= 1; ++persistent)
+    for (int bsz : blocks)
+      for (int pt = 1; pt <= (persistent ? 1 : 2); ++pt) {
+        rrmhd_tuning t = cur_best;
+        t.face_block = bsz;
+        t.face_per_thread = pt;
+        t.face_persistent = persistent;
+        consider(t);
+      }
+  // 3. lanes
+  for (int lanes : {1, 2, 4, 8, 16, 32}) {
+    if (lanes > n) break;
+    rrmhd_tuning t = cur_best;
+    t.lanes = lanes;
+    consider(t);
+  }
+  if (rc == RRMHD_OK) rc = rrmhd_set_tuning(c, &cur_best);
+  if (rc == RRMHD_OK) rc = cuda_check(c, copy_state(false), "autotune restore");
+  if (rc == RRMHD_OK) rc = cuda_check(c, cudaStreamSynchronize(st), "autotune sync");
+  release();
+  if (rc != RRMHD_OK) return rc;
+  if (best) *best = cur_best;
+  if (best_ms) *best_ms = cur_ms;
+  return RRMHD_OK;
 }
 
 const char* rrmhd_last_error(const rrmhd_ctx* c) { return c ? c->err.c_str() : "null context"; }

@@ -9,6 +9,7 @@
 
 #include "batch.h"
 #include "batch_index.cuh"
+#include "launch_shape.cuh"
 #include "physics_f32.cuh"
 #include "scheme_f64.cuh"
 
@@ -37,10 +38,9 @@ __device__ __forceinline__ void load12f(const double* __restrict__ A, int64_t st
   for (int k = 0; k < NV; ++k) x[k] = (float)__ldg(A + k * stride + c);
 }
 
-__global__ void __launch_bounds__(kFaceThreads) k_faces_f32(StageArgs a) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Face t of the launch's face ranges, in FP32.
+static __device__ __noinline__ void face_item_f32(const StageArgs& a, int64_t t) {
   const Batch& b = a.b;
-  if (t >= lane_faces(b)) return;
   const int64_t g = lane_face(b, t);
   const FacePos fp = face_pos(b, g);
   if (a.check_active && !inst_active(b, fp.i)) return;
@@ -137,9 +137,7 @@ __device__ __forceinline__ void store_cell(const StageArgs& a, int64_t c, const 
   }
 }
 
-__global__ void __launch_bounds__(kCellThreads) k_cells_f32(StageArgs a) {
-  const int64_t c = a.b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= a.b.c_end) return;
+static __device__ __noinline__ void cell_item_f32(const StageArgs& a, int64_t c) {
   const CellPos q = cell_pos(a.b, c);
   if (!inst_active(a.b, q.i)) return;
   double Un[NV], Vn[NV];
@@ -153,6 +151,27 @@ __global__ void __launch_bounds__(kCellThreads) k_cells_f32(StageArgs a) {
     return;
   }
   store_cell(a, c, Un, Vn);
+}
+
+template <int BS, int PT>
+__global__ void __launch_bounds__(BS) k_faces_f32(StageArgs a) {
+  grid_items<BS, PT>(lane_faces(a.b), [&](int64_t t) { face_item_f32(a, t); });
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS) k_faces_f32_persistent(StageArgs a) {
+  persistent_items(lane_faces(a.b), a.work, [&](int64_t t) { face_item_f32(a, t); });
+}
+
+template <int BS, int PT>
+__global__ void __launch_bounds__(BS) k_cells_f32(StageArgs a) {
+  grid_items<BS, PT>(a.b.c_end - a.b.c_begin, [&](int64_t t) { cell_item_f32(a, a.b.c_begin + t); });
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS) k_cells_f32_persistent(StageArgs a) {
+  persistent_items(a.b.c_end - a.b.c_begin, a.work + 1,
+                   [&](int64_t t) { cell_item_f32(a, a.b.c_begin + t); });
 }
 
 __global__ void __launch_bounds__(kFaceThreads) k_fallback_faces_f32(StageArgs a) {
@@ -233,16 +252,67 @@ __global__ void k_widen(const float* __restrict__ F32, int64_t fs32, int64_t f_b
 
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-}  // namespace
+// Resident blocks per SM of the persistent kernels ([0] faces, [1] cells; by
+// block size index 0..3), resolved by prepare_launch_shapes().
+int g_resident[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+int g_sms = 0;
 
-void launch_faces_f32(const StageArgs& a, cudaStream_t s) {
-  const int64_t n = a.b.f_count[0] + a.b.f_count[1] + a.b.f_count[2];
-  if (n > 0) k_faces_f32<<<grid_for(n, kFaceThreads), kFaceThreads, 0, s>>>(a);
+inline int bs_index(int B) { return B == 32 ? 0 : B == 64 ? 1 : B == 128 ? 2 : 3; }
+
+inline unsigned persistent_grid(int64_t n, int B, int kind) {
+  const int per_sm = g_resident[kind][bs_index(B)] > 0 ? g_resident[kind][bs_index(B)] : 1;
+  const int64_t resident = (int64_t)(g_sms > 0 ? g_sms : 1) * per_sm;
+  const int64_t needed = (n + B - 1) / B;
+  return (unsigned)(needed < resident ? needed : resident);
 }
 
-void launch_cells_f32(const StageArgs& a, cudaStream_t s) {
+}  // namespace
+
+bool prepare_launch_shapes_f32() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+  bool ok = true;
+#define X(B)                                                                                    \
+  ok = ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_resident[0][bs_index(B)],         \
+                                                          k_faces_f32_persistent<B>, B, 0) == cudaSuccess; \
+  ok = ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_resident[1][bs_index(B)],         \
+                                                          k_cells_f32_persistent<B>, B, 0) == cudaSuccess;
+  RR_PERSISTENT_BLOCKS(X)
+#undef X
+  return ok;
+}
+
+void launch_faces_f32(const StageArgs& a, const LaunchShape& sh, cudaStream_t s) {
+  const int64_t n = a.b.f_count[0] + a.b.f_count[1] + a.b.f_count[2];
+  if (n <= 0) return;
+  if (sh.persistent) {
+    cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);
+#define X(B) \
+    if (sh.block == B) { k_faces_f32_persistent<B><<<persistent_grid(n, B, 0), B, 0, s>>>(a); return; }
+    RR_PERSISTENT_BLOCKS(X)
+#undef X
+  }
+#define X(B, T) \
+  if (sh.block == B && sh.per_thread == T) { k_faces_f32<B, T><<<grid_for(n, B * T), B, 0, s>>>(a); return; }
+  RR_GRID_SHAPES(X)
+#undef X
+}
+
+void launch_cells_f32(const StageArgs& a, const LaunchShape& sh, cudaStream_t s) {
   const int64_t n = a.b.c_end - a.b.c_begin;
-  if (n > 0) k_cells_f32<<<grid_for(n, kCellThreads), kCellThreads, 0, s>>>(a);
+  if (n <= 0) return;
+  if (sh.persistent) {
+    cudaMemsetAsync(a.work + 1, 0, sizeof(unsigned long long), s);
+#define X(B) \
+    if (sh.block == B) { k_cells_f32_persistent<B><<<persistent_grid(n, B, 1), B, 0, s>>>(a); return; }
+    RR_PERSISTENT_BLOCKS(X)
+#undef X
+  }
+#define X(B, T) \
+  if (sh.block == B && sh.per_thread == T) { k_cells_f32<B, T><<<grid_for(n, B * T), B, 0, s>>>(a); return; }
+  RR_GRID_SHAPES(X)
+#undef X
 }
 
 void launch_fallback_f32(const StageArgs& a, cudaStream_t s) {

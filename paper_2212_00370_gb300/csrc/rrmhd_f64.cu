@@ -17,6 +17,7 @@
 
 #include "batch.h"
 #include "batch_index.cuh"
+#include "launch_shape.cuh"
 #include "scheme_f64.cuh"
 
 namespace rr {
@@ -35,10 +36,9 @@ constexpr int kCellThreads = 128;
 #define RR_CELL_MIN_BLOCKS 1
 #endif
 
-__global__ void __launch_bounds__(kFaceThreads, RR_FACE_MIN_BLOCKS) k_faces(StageArgs a) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Face t of the launch's face ranges: stencil, PLM + fallback, PVM-int-8 flux.
+static __device__ __noinline__ void face_item(const StageArgs& a, int64_t t) {
   const Batch& b = a.b;
-  if (t >= lane_faces(b)) return;
   const int64_t g = lane_face(b, t);
   const FacePos fp = face_pos(b, g);
   if (a.check_active && !inst_active(b, fp.i)) return;
@@ -143,9 +143,7 @@ __device__ __forceinline__ void store_cell(const StageArgs& a, int64_t c, const 
 }
 
 // Pass 1: every cell.  A cell whose U* is inadmissible is only flagged.
-__global__ void __launch_bounds__(kCellThreads, RR_CELL_MIN_BLOCKS) k_cells(StageArgs a) {
-  const int64_t c = a.b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= a.b.c_end) return;
+static __device__ __noinline__ void cell_item(const StageArgs& a, int64_t c) {
   const CellPos q = cell_pos(a.b, c);
   if (!inst_active(a.b, q.i)) return;
   double Un[NV], Vn[NV];
@@ -159,6 +157,27 @@ __global__ void __launch_bounds__(kCellThreads, RR_CELL_MIN_BLOCKS) k_cells(Stag
     return;
   }
   store_cell(a, c, Un, Vn);
+}
+
+template <int BS, int PT>
+__global__ void __launch_bounds__(BS, RR_FACE_MIN_BLOCKS) k_faces(StageArgs a) {
+  grid_items<BS, PT>(lane_faces(a.b), [&](int64_t t) { face_item(a, t); });
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS, 1) k_faces_persistent(StageArgs a) {
+  persistent_items(lane_faces(a.b), a.work, [&](int64_t t) { face_item(a, t); });
+}
+
+template <int BS, int PT>
+__global__ void __launch_bounds__(BS, RR_CELL_MIN_BLOCKS) k_cells(StageArgs a) {
+  grid_items<BS, PT>(a.b.c_end - a.b.c_begin, [&](int64_t t) { cell_item(a, a.b.c_begin + t); });
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS, 1) k_cells_persistent(StageArgs a) {
+  persistent_items(a.b.c_end - a.b.c_begin, a.work + 1,
+                   [&](int64_t t) { cell_item(a, a.b.c_begin + t); });
 }
 
 // Admissibility fallback, faces: first-order Rusanov flux at every face next
@@ -333,18 +352,68 @@ __global__ void k_implicit(Params P, Batch b, double hdt, const double* __restri
 
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-}  // namespace
+// Resident blocks per SM of the persistent kernels ([0] faces, [1] cells; by
+// block size index 0..3), resolved by prepare_launch_shapes().
+int g_resident[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+int g_sms = 0;
 
-void launch_faces_f64(const StageArgs& a, cudaStream_t s) {
-  const int64_t n = a.b.f_count[0] + a.b.f_count[1] + a.b.f_count[2];
-  if (n <= 0) return;
-  k_faces<<<grid_for(n, kFaceThreads), kFaceThreads, 0, s>>>(a);
+inline int bs_index(int B) { return B == 32 ? 0 : B == 64 ? 1 : B == 128 ? 2 : 3; }
+
+// Blocks of a persistent launch: the resident grid, or fewer when n is small.
+inline unsigned persistent_grid(int64_t n, int B, int kind) {
+  const int per_sm = g_resident[kind][bs_index(B)] > 0 ? g_resident[kind][bs_index(B)] : 1;
+  const int64_t resident = (int64_t)(g_sms > 0 ? g_sms : 1) * per_sm;
+  const int64_t needed = (n + B - 1) / B;
+  return (unsigned)(needed < resident ? needed : resident);
 }
 
-void launch_cells_f64(const StageArgs& a, cudaStream_t s) {
+}  // namespace
+
+bool prepare_launch_shapes_f64() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+  bool ok = true;
+#define X(B)                                                                                   \
+  ok = ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_resident[0][bs_index(B)],        \
+                                                          k_faces_persistent<B>, B, 0) == cudaSuccess; \
+  ok = ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_resident[1][bs_index(B)],        \
+                                                          k_cells_persistent<B>, B, 0) == cudaSuccess;
+  RR_PERSISTENT_BLOCKS(X)
+#undef X
+  return ok;
+}
+
+void launch_faces_f64(const StageArgs& a, const LaunchShape& sh, cudaStream_t s) {
+  const int64_t n = a.b.f_count[0] + a.b.f_count[1] + a.b.f_count[2];
+  if (n <= 0) return;
+  if (sh.persistent) {
+    cudaMemsetAsync(a.work, 0, sizeof(unsigned long long), s);
+#define X(B) \
+    if (sh.block == B) { k_faces_persistent<B><<<persistent_grid(n, B, 0), B, 0, s>>>(a); return; }
+    RR_PERSISTENT_BLOCKS(X)
+#undef X
+  }
+#define X(B, T) \
+  if (sh.block == B && sh.per_thread == T) { k_faces<B, T><<<grid_for(n, B * T), B, 0, s>>>(a); return; }
+  RR_GRID_SHAPES(X)
+#undef X
+}
+
+void launch_cells_f64(const StageArgs& a, const LaunchShape& sh, cudaStream_t s) {
   const int64_t n = a.b.c_end - a.b.c_begin;
   if (n <= 0) return;
-  k_cells<<<grid_for(n, kCellThreads), kCellThreads, 0, s>>>(a);
+  if (sh.persistent) {
+    cudaMemsetAsync(a.work + 1, 0, sizeof(unsigned long long), s);
+#define X(B) \
+    if (sh.block == B) { k_cells_persistent<B><<<persistent_grid(n, B, 1), B, 0, s>>>(a); return; }
+    RR_PERSISTENT_BLOCKS(X)
+#undef X
+  }
+#define X(B, T) \
+  if (sh.block == B && sh.per_thread == T) { k_cells<B, T><<<grid_for(n, B * T), B, 0, s>>>(a); return; }
+  RR_GRID_SHAPES(X)
+#undef X
 }
 
 void launch_fallback_f64(const StageArgs& a, cudaStream_t s) {

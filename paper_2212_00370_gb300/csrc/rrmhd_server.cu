@@ -136,6 +136,8 @@ struct rrmhd_server {
   rr::DeviceBufs B;
   double *kap[2] = {nullptr, nullptr}, *sig[2] = {nullptr, nullptr}, *jcb[2] = {nullptr, nullptr};
   int64_t* d_src_off = nullptr;
+  unsigned long long* work = nullptr;  // chunk counters, 2 per lane
+  rr::Tuning tune;                     // launch shapes
   int kc = 0;   // live copy of kappa / sigma / jc
   int cur = 0;  // the state lives in (U0,V0) when 0, in (Ua,Va) when 1
   cudaStream_t stream = nullptr;
@@ -287,8 +289,9 @@ bool step(rrmhd_server* s, std::vector<rrmhd_result>& finished, int64_t& zone_up
   for (size_t l = 0; l < ranges.size(); ++l) {
     const LaneRt& ln = s->lanes[l];
     SRV_CUDA(s, cudaStreamWaitEvent(ln.stream, s->fork, 0));
-    rr::enqueue_step(s->P, s->opts.precision, s->B,
-                     rr::make_batch(L, s->B, ranges[l].first, ranges[l].second), s->cur, ln.stream);
+    rr::enqueue_step(s->P, s->opts.precision, s->tune, s->B,
+                     rr::make_batch(L, s->B, ranges[l].first, ranges[l].second), s->cur,
+                     s->work + 2 * l, ln.stream);
     SRV_CUDA(s, cudaGetLastError());
     SRV_CUDA(s, cudaEventRecord(ln.done, ln.stream));
   }
@@ -447,7 +450,7 @@ void free_server(rrmhd_server* s) {
   void* bufs[] = {B.inst,    B.cell_off, B.face_off, B.U0,      B.Ua,      B.Ub,
                   B.V0,      B.Va,       B.Vb,       B.Fhat,    B.bad,     B.t,
                   B.t_end,   B.dt,       B.smax,     B.status,  s->kap[0], s->kap[1],
-                  s->sig[0], s->sig[1],  s->jcb[0],  s->jcb[1], s->d_src_off};
+                  s->sig[0], s->sig[1],  s->jcb[0],  s->jcb[1], s->d_src_off, s->work};
   for (void* p : bufs)
     if (p) cudaFree(p);
   void* hbufs[] = {s->h_t, s->h_tend, s->h_smax, s->h_status};
@@ -480,9 +483,22 @@ rrmhd_status rrmhd_server_create(const rrmhd_opts* opts, const rrmhd_server_conf
   rrmhd_server_config c{};
   if (cfg) c = *cfg;
   if (c.mem_bytes < 0 || c.max_resident_cells < 0 || c.max_resident < 0) return RRMHD_EINVAL;
+  const rrmhd_tuning& tu = c.tuning;
+  const bool tuned = tu.face_block || tu.cell_block || tu.lanes;
+  rr::Tuning tune = rr::default_tuning();
+  int lanes = opts->lanes;
+  if (tuned) {
+    tune.faces = {tu.face_block, tu.face_per_thread, tu.face_persistent};
+    tune.cells = {tu.cell_block, tu.cell_per_thread, tu.cell_persistent};
+    lanes = tu.lanes;
+    if (!rr::tuning_ok(tune) || lanes < 1) return RRMHD_EINVAL;
+  }
+  if (!rr::prepare_launch_shapes()) return RRMHD_ECUDA;
 
   rrmhd_server* s = new rrmhd_server();
   s->opts = *opts;
+  s->opts.lanes = lanes;
+  s->tune = tune;
   s->P = rr::make_params(*opts);
   s->t0 = Clock::now();
   auto fail = [&](rrmhd_status st) {
@@ -526,6 +542,7 @@ rrmhd_status rrmhd_server_create(const rrmhd_opts* opts, const rrmhd_server_conf
   A((void**)&B.smax, sizeof(unsigned long long) * I);
   A((void**)&B.status, sizeof(int) * I);
   A((void**)&s->d_src_off, sizeof(int64_t) * I);
+  A((void**)&s->work, sizeof(unsigned long long) * 2 * lanes);
   if (!ok) {
     cudaGetLastError();  // clear the allocation error
     return fail(RRMHD_ENOMEM);
@@ -541,7 +558,7 @@ rrmhd_status rrmhd_server_create(const rrmhd_opts* opts, const rrmhd_server_conf
   if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess)
     return fail(RRMHD_ECUDA);
-  s->lanes.resize(opts->lanes);
+  s->lanes.resize(lanes);
   for (LaneRt& l : s->lanes)
     if (cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming) != cudaSuccess)

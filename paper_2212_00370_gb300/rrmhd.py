@@ -34,8 +34,25 @@ class rrmhd_opts(C.Structure):
                 ("imp_tol", C.c_double), ("lanes", C.c_int)]
 
 
+class rrmhd_tuning(C.Structure):
+    _fields_ = [(k, C.c_int) for k in ("face_block", "face_per_thread", "face_persistent", "cell_block",
+                                       "cell_per_thread", "cell_persistent", "lanes")]
+
+
+def tuning_dict(t):
+    return {f: getattr(t, f) for f, _ in rrmhd_tuning._fields_}
+
+
+def make_tuning(**kw):
+    t = rrmhd_tuning(128, 1, 0, 128, 1, 0, 8)
+    for k, v in kw.items():
+        setattr(t, k, int(v))
+    return t
+
+
 class rrmhd_server_config(C.Structure):
-    _fields_ = [("mem_bytes", C.c_int64), ("max_resident_cells", C.c_int64), ("max_resident", C.c_int)]
+    _fields_ = [("mem_bytes", C.c_int64), ("max_resident_cells", C.c_int64), ("max_resident", C.c_int),
+                ("tuning", rrmhd_tuning)]
 
 
 class rrmhd_result(C.Structure):
@@ -86,6 +103,9 @@ _SIGNATURES = [
     ("rrmhd_prim_z", C.c_int, [_VP, _VP, _VP, _I64]),
     ("rrmhd_profile_step", C.c_int, [_VP, _DP]),
     ("rrmhd_launches_per_step", C.c_int, [_VP]),
+    ("rrmhd_get_tuning", C.c_int, [_VP, C.POINTER(rrmhd_tuning)]),
+    ("rrmhd_set_tuning", C.c_int, [_VP, C.POINTER(rrmhd_tuning)]),
+    ("rrmhd_autotune", C.c_int, [_VP, C.c_int, C.POINTER(rrmhd_tuning), _DP]),
     ("rrmhd_cfl_dt_noalloc", C.c_int, [C.POINTER(rrmhd_grid), C.POINTER(rrmhd_opts), _VP, _VP, _VP]),
     ("rrmhd_server_create", C.c_int, [C.POINTER(rrmhd_opts), C.POINTER(rrmhd_server_config),
                                       C.POINTER(_VP)]),
@@ -248,6 +268,26 @@ class Context:
     def launches_per_step(self):
         return lib().rrmhd_launches_per_step(self.ctx)
 
+    def get_tuning(self):
+        t = rrmhd_tuning()
+        _check(self.ctx, lib().rrmhd_get_tuning(self.ctx, C.byref(t)))
+        return tuning_dict(t)
+
+    def set_tuning(self, **kw):
+        t = rrmhd_tuning()
+        _check(self.ctx, lib().rrmhd_get_tuning(self.ctx, C.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        _check(self.ctx, lib().rrmhd_set_tuning(self.ctx, C.byref(t)))
+
+    def autotune(self, repeats=1):
+        """Times launch shapes on real steps from the current state (restored after);
+        keeps and returns the fastest (dict) and its median step time in ms."""
+        t = rrmhd_tuning()
+        ms = C.c_double()
+        _check(self.ctx, lib().rrmhd_autotune(self.ctx, int(repeats), C.byref(t), C.byref(ms)))
+        return tuning_dict(t), ms.value
+
     def imex_step(self, nsteps=1):
         _check(self.ctx, lib().rrmhd_imex_step(self.ctx, int(nsteps)))
 
@@ -310,9 +350,12 @@ class Server:
     """A librrmhd serving loop: requests are submitted from host arrays and run to
     completion on the current device with continuous batching."""
 
-    def __init__(self, mem_bytes=0, max_resident_cells=0, max_resident=0, **opts):
+    def __init__(self, mem_bytes=0, max_resident_cells=0, max_resident=0, tuning=None, **opts):
+        """tuning: a dict of rrmhd_tuning fields (e.g. from Context.autotune), or None."""
         self.opts = make_opts(**opts)
         cfg = rrmhd_server_config(int(mem_bytes), int(max_resident_cells), int(max_resident))
+        if tuning:
+            cfg.tuning = make_tuning(**tuning)
         self.srv = C.c_void_p()
         rc = lib().rrmhd_server_create(C.byref(self.opts), C.byref(cfg), C.byref(self.srv))
         if rc != 0:

@@ -55,6 +55,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"rrmhd_grid": rrmhd.rrmhd_grid, "rrmhd_opts": rrmhd.rrmhd_opts,
+               "rrmhd_tuning": rrmhd.rrmhd_tuning,
                "rrmhd_server_config": rrmhd.rrmhd_server_config,
                "rrmhd_result": rrmhd.rrmhd_result, "rrmhd_server_stats": rrmhd.rrmhd_server_stats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rrmhd.h"', "int main(void) {"]
