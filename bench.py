@@ -38,10 +38,11 @@ sys.path.insert(0, ROOT)
 # measured with ncu on a 2048-instance sample of the same distribution
 # (profiles/c1_fp64_k_cells_k_faces.md).
 FP64_INST_PER_ZONE = {"fp64": {"faces": 5640.0, "cells": 5439.0},
-                      "fp32_bulk": {"faces": None, "cells": 4299.0}}
+                      "fp32_bulk": {"faces": None, "cells": 4299.0},
+                      "fp64_tangent": {"faces": None, "cells": 5439.0}}
 # DRAM bytes per cell of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
 TRAFFIC_PER_CELL = {"fp64": {"faces": 240.0, "cells": 1033.0},
-                    "fp32_bulk": {"faces": 167.0, "cells": 935.0}}
+                    "fp32_bulk": {"faces": 167.0, "cells": 935.0}, "fp64_tangent": {}}
 # Nominal FP64 rate of GB300: 1.25 TFLOP/s = 6.25e11 FP64-pipe instructions/s
 # (2 per SM per clock on 152 SMs at 2.07 GHz); no MEASURED_PEAKS entry exists for FP64.
 FP64_PEAK_INST = 6.25e11
@@ -60,8 +61,9 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=4096,
                    help="instances in the CPU sample (1 step each; default: the whole batch)")
     p.add_argument("--lanes", type=int, default=8, help="independent sub-batches (streams)")
-    p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32_bulk"],
-                   help="both: FP32-bulk is the headline value, FP64 reported beside it")
+    p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32_bulk", "fp64_tangent"],
+                   help="both: FP32-bulk is the headline value, FP64 (and FP64 with tangent "
+                        "products) reported beside it")
     p.add_argument("--serve-requests", type=int, default=32,
                    help="requests of the C4 serving sample (0: skip the serving measurement)")
     p.add_argument("--serve-cells", type=int, default=4_000_000,
@@ -180,8 +182,9 @@ def measure(a, precision, rank, world, local):
     seed = W.SEED_BASE + 1 + rank
     w = W.riemann_batch(a.instances, seed=seed)
     grids = [rrmhd.make_grid(1, g["n"], g["dx"], g["bc"]) for g in w.grids]
+    extra = {"pvm_products": 1} if precision == "fp64_tangent" else {}
     ctx = rrmhd.Context(grids, gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl, lanes=a.lanes,
-                        precision=precision)
+                        precision="fp64" if precision == "fp64_tangent" else precision, **extra)
     ctx.set_opacity(torch.tensor(w.kappa, device="cuda"), torch.tensor(w.sigma, device="cuda"))
     ctx.set_state(torch.tensor(w.V, device="cuda"))
     ctx.set_times(np.zeros(w.n_inst), np.full(w.n_inst, np.inf))
@@ -192,15 +195,12 @@ def measure(a, precision, rank, world, local):
         if world > 1:
             dist.barrier()
 
+    if a.tuning:                             # fixed shapes from the first step on
+        ctx.set_tuning(**json.loads(a.tuning))
     ctx.imex_step(max(a.warmup, 2))          # warm-up (also builds the step graphs)
     torch.cuda.synchronize()
     tuning, tune_ms = ctx.get_tuning(), None
-    if a.tuning:
-        ctx.set_tuning(**json.loads(a.tuning))
-        tuning = ctx.get_tuning()
-        ctx.imex_step(1)
-        torch.cuda.synchronize()
-    elif not a.no_autotune:                  # untimed: shapes chosen on this state, state restored
+    if not (a.tuning or a.no_autotune):      # untimed: shapes chosen on this state, state restored
         t0 = time.perf_counter()
         tuning, tune_ms = ctx.autotune(repeats=1)
         tune_s = time.perf_counter() - t0
@@ -349,7 +349,7 @@ def measure_serving(a, tuning=None):
     }
 
 
-DTYPE = {"fp64": "f64", "fp32_bulk": "f32 faces + f64 cells"}
+DTYPE = {"fp64": "f64", "fp32_bulk": "f32 faces + f64 cells", "fp64_tangent": "f64"}
 
 
 def run_ours(a, rank, world, pool, cores):
@@ -357,7 +357,7 @@ def run_ours(a, rank, world, pool, cores):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    precisions = ["fp32_bulk", "fp64"] if a.precision == "both" else [a.precision]
+    precisions = ["fp32_bulk", "fp64", "fp64_tangent"] if a.precision == "both" else [a.precision]
     res = {p: measure(a, p, rank, world, local) for p in precisions}
     head = res[precisions[0]]
     out = {
@@ -386,6 +386,13 @@ def run_ours(a, rank, world, pool, cores):
                        "failed_instances": f["failed"], "clocks": f["clocks"]}
         out["fp32_bulk_speedup_over_fp64"] = head["value"] / f["value"]
         out["gpu_launches"] += f["gpu_launches"]
+        g = res["fp64_tangent"]
+        out["fp64_tangent"] = {"value": g["value"], "ms_per_step": g["ms_per_step"], "p50_ms": g["p50_ms"],
+                               "p99_ms": g["p99_ms"], "launch_shapes": g["tuning"],
+                               "failed_instances": g["failed"], "e2e": g["e2e"],
+                               "note": "FP64 with exact tangent Jacobian products instead of the "
+                                       "paper's eps = 1e-8 flux differences (a variant)"}
+        out["gpu_launches"] += g["gpu_launches"]
     if a.serve_requests > 0 and world == 1:
         out["serving"] = measure_serving(a, res["fp32_bulk"]["tuning"] if "fp32_bulk" in res else None)
     if rank == 0 and pool is not None:

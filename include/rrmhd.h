@@ -79,6 +79,15 @@ typedef struct {
     int    lanes;      /* independent sub-batches stepped on their own streams (8); the
                           instances are split into contiguous ranges of about equal cell
                           count, so one range's slow cells overlap the others' work     */
+    int    pvm_k;      /* PVM-int-n with n = 2^pvm_k (Eq. iterat): 3 = PVM-int-8, the paper's
+                          solver (4 A^2 products per face, default); 4 = PVM-int-16 (8)  */
+    int    pvm_products; /* how the FP64 form takes the Jacobian products A w of the PVM
+                          viscosity: 0 = nested flux differences with eps = pvm_eps, the
+                          paper's (Eq. utilde; default; bit-reproducible against the
+                          reference arithmetic); 1 = exact tangent (dual-number) products,
+                          the root of con2prim differentiated by the implicit-function
+                          theorem: no Newton iteration per product.  The FP32-bulk form
+                          always uses tangent products (eps is below FP32 resolution). */
 } rrmhd_opts;
 
 typedef struct rrmhd_ctx rrmhd_ctx;

@@ -32,7 +32,7 @@ class _Params(C.Structure):
     _fields_ = [
         ("gamma", C.c_double), ("a_rad", C.c_double), ("cfl", C.c_double),
         ("pvm_eps", C.c_double), ("recon", C.c_int), ("beta_mode", C.c_int),
-        ("imp_mode", C.c_int), ("c2p_maxit", C.c_int), ("imp_maxit", C.c_int),
+        ("imp_mode", C.c_int), ("pvm_k", C.c_int), ("c2p_maxit", C.c_int), ("imp_maxit", C.c_int),
         ("imp_tol", C.c_double), ("gfac", C.c_double), ("gm1g", C.c_double),
     ]
 
@@ -62,10 +62,11 @@ class Params:
     c2p_maxit: int = 60
     imp_maxit: int = 50
     imp_tol: float = 1e-10
+    pvm_k: int = 3          # PVM-int-2^k: 3 is the paper's PVM-int-8, 4 is PVM-int-16
 
     def struct(self):
         p = _Params(self.gamma, self.a_rad, self.cfl, self.pvm_eps, RECON[self.recon],
-                    1 if self.beta else 0, 0 if self.implicit == "newton" else 1,
+                    1 if self.beta else 0, 0 if self.implicit == "newton" else 1, self.pvm_k,
                     self.c2p_maxit, self.imp_maxit, self.imp_tol, 0.0, 0.0)
         lib().or_params_init(C.byref(p))
         return p
@@ -114,6 +115,7 @@ def lib():
             "or_m1_pressure": (None, [C.c_double, dp, dp]),
             "or_eddington_factor": (C.c_double, [C.c_double]),
             "or_limiter": (C.c_double, [C.c_int, C.c_double, C.c_double]),
+            "or_pvm_coefficients": (C.c_int, [C.c_int, dp]),
             "or_reconstruct": (None, [P, dp, dp, dp, dp, dp, C.POINTER(C.c_int)]),
             "or_picard_matrix": (None, [C.c_double, C.c_double, C.c_double, C.c_double, dp,
                                         C.c_double, C.c_double, dp, dp, dp, dp]),
@@ -251,6 +253,13 @@ def m1_pressure(E, F):
 
 def eddington_factor(f):
     return lib().or_eddington_factor(float(f))
+
+
+def pvm_coefficients(k):
+    """Horner-order coefficients of p_k from Eq. iterat (degree 2^(k-1) in x^2)."""
+    a = np.zeros(9)
+    m = lib().or_pvm_coefficients(int(k), _d(a))
+    return a[:m + 1]
 
 
 def limiter(recon, dL, dR):

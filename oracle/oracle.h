@@ -49,6 +49,7 @@ typedef struct {
     int    recon;      /* OR_RECON_*                                               */
     int    beta_mode;  /* 1: beta = min(1/tau_L, 1/tau_R, 1) (Eq. beta); 0: beta=1  */
     int    imp_mode;   /* OR_IMP_NEWTON (default) or OR_IMP_PICARD (paper's C matrix) */
+    int    pvm_k;      /* PVM-int-n with n = 2^k (Eq. iterat): 3 (PVM-int-8), 4 (-16) */
     int    c2p_maxit;  /* Newton iterations allowed in con2prim                    */
     int    imp_maxit;  /* outer iterations allowed in the implicit solve           */
     double imp_tol;    /* implicit convergence: max|dX| <= imp_tol * E_r           */
@@ -81,6 +82,7 @@ void   or_four_force(double kappa, double sigma, double rho, const double u[3], 
 
 /* ---- scheme (scheme.c) ---- */
 double or_limiter(int recon, double dL, double dR);
+int    or_pvm_coefficients(int k, double alpha[9]);   /* Horner-order coefficients of p_k */
 void   or_reconstruct(const or_params* P, const double Vm1[12], const double V0[12],
                       const double Vp1[12], double Vminus[12], double Vplus[12], int* fallback);
 int    or_pvm_flux(const or_params* P, int dir, const double VL[12], const double VR[12],

@@ -57,9 +57,36 @@ void or_reconstruct(const or_params* P, const double Vm1[12], const double V0[12
     if (fallback) *fallback = bad;
 }
 
-/* Coefficients of p_3(x) = x^2(x^2(x^2(a0 x^2 + a1) + a2) + a3) + a4, the
- * internal approximation of |x| on [-1,1] built by Eq. iterat with k = 3. */
-static const double ALPHA[5] = {-1.0 / 128.0, 3.0 / 32.0, -23.0 / 64.0, 31.0 / 32.0, 39.0 / 128.0};
+/* Coefficients of the internal approximation p_k of |x| on [-1,1] built by
+ * Eq. iterat: p_0 = 1, p_k = (2 p_{k-1} - p_{k-1}^2 + x^2)/2, a polynomial of
+ * degree m = 2^(k-1) in y = x^2.  alpha[0..m] are its coefficients in Horner
+ * order (highest degree first): p_k = (...(alpha_0 y + alpha_1) y + ...) y + alpha_m.
+ * For k = 3 these are the printed -1/128, 3/32, -23/64, 31/32, 39/128.  All
+ * coefficients are dyadic rationals, exact in double for k <= 4.  Returns m,
+ * or 0 for k outside 1..4. */
+int or_pvm_coefficients(int k, double alpha[9])
+{
+    if (k < 1 || k > 4) return 0;
+    double c[17] = {1.0};   /* ascending powers of y; p_0 = 1 */
+    int deg = 0;
+    for (int j = 1; j <= k; j++) {
+        double sq[17] = {0.0};
+        for (int a = 0; a <= deg; a++)
+            for (int b = 0; b <= deg; b++) sq[a + b] += c[a] * c[b];
+        int nd = 2 * deg > 1 ? 2 * deg : 1;
+        double nc[17] = {0.0};
+        for (int a = 0; a <= nd; a++) {
+            double v = -sq[a];
+            if (a <= deg) v += 2.0 * c[a];
+            if (a == 1) v += 1.0;
+            nc[a] = 0.5 * v;
+        }
+        for (int a = 0; a <= nd; a++) c[a] = nc[a];
+        deg = nd;
+    }
+    for (int a = 0; a <= deg; a++) alpha[a] = c[deg - a];
+    return deg;
+}
 
 typedef struct {
     const or_params* P;
@@ -87,10 +114,12 @@ static int a2_product(pvm_ctx* c, const double w[12], double out[12])
     return 0;
 }
 
-/* PVM-int-8 numerical flux at one interface (Sec. 3.2.2, steps 1-7):
- *   F^ = (F_L + F_R)/2 - beta U_{k+1}/2,  U_{k+1} ~ p_3(A(U_m)) (U_R - U_L),
- * with lambda_max = 1, the Horner recursion in A^2
- *   U_1 = a0 A^2 U_0 + a1 U_0,  U_{l+1} = A^2 U_l + a_{l+1} U_0  (l = 1..3),
+/* PVM-int-n numerical flux at one interface (Sec. 3.2.2, steps 1-7), n = 2^k:
+ *   F^ = (F_L + F_R)/2 - beta U_{m}/2,  U_{m} ~ p_k(A(U_m)) (U_R - U_L),
+ * with lambda_max = 1 and the Horner recursion in A^2 (m = 2^(k-1) products)
+ *   U_1 = a0 A^2 U_0 + a1 U_0,  U_{l+1} = A^2 U_l + a_{l+1} U_0  (l = 1..m-1).
+ * k = 3 (PVM-int-8) is the paper's solver: four products, U_4 = U_{k+1}.  k = 4
+ * (PVM-int-16) is the variant the paper reports testing.
  * and beta = min{1/tau_L, 1/tau_R, 1} (Eq. beta), tau = rho W (kappa + sigma) dx
  * at the two cell centres adjacent to the face.
  * If a con2prim inside the viscosity term fails, the face uses Q = I
@@ -121,20 +150,22 @@ int or_pvm_flux(const or_params* P, int dir, const double VL[12], const double V
         beta = 1.0 / t;
     }
 
+    double alpha[9];
+    const int m = or_pvm_coefficients(P->pvm_k, alpha);   /* A^2 products needed */
     double Ul[12], Y[12];
     int fail = 0;
-    if (or_con2prim(P, c.Um, Zg, Vm, &c.Zm, st) != OR_OK) {
+    if (m == 0 || or_con2prim(P, c.Um, Zg, Vm, &c.Zm, st) != OR_OK) {
         fail = 1;
     } else {
         or_flux(P, dir, Vm, c.Um, c.Fm);
         if (st) st->flux_evals++;
         for (int k = 0; k < 12; k++) Ul[k] = U0[k];
-        for (int l = 0; l < 4 && !fail; l++) {
+        for (int l = 0; l < m && !fail; l++) {
             if (a2_product(&c, Ul, Y)) { fail = 1; break; }
             if (l == 0)
-                for (int k = 0; k < 12; k++) Ul[k] = ALPHA[0] * Y[k] + ALPHA[1] * U0[k];
+                for (int k = 0; k < 12; k++) Ul[k] = alpha[0] * Y[k] + alpha[1] * U0[k];
             else
-                for (int k = 0; k < 12; k++) Ul[k] = Y[k] + ALPHA[l + 1] * U0[k];
+                for (int k = 0; k < 12; k++) Ul[k] = Y[k] + alpha[l + 1] * U0[k];
         }
     }
     if (fail) {

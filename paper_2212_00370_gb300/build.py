@@ -27,7 +27,7 @@ UNITS = {
     "rrmhd_f32.cu": [],
     "rrmhd_server.cu": ["--fmad=false"],
 }
-HEADERS = ["physics_f64.cuh", "scheme_f64.cuh", "physics_f32.cuh", "batch.h", "batch_index.cuh",
+HEADERS = ["physics_f64.cuh", "scheme_f64.cuh", "physics_tangent.cuh", "batch.h", "batch_index.cuh",
            "engine.h"]
 
 

@@ -31,6 +31,8 @@ enum Recon : int { RECON_GODUNOV = 0, RECON_MINMOD = 1, RECON_MC = 2, RECON_VANL
 struct Params {
   double gamma, a_rad, cfl, pvm_eps;
   int recon, beta_mode, c2p_maxit, imp_maxit;
+  int pvm_k;  // PVM-int-2^k: 3 (PVM-int-8) or 4 (PVM-int-16)
+  int pvm_products;  // FP64 A w products: 0 nested flux differences (Eq. utilde), 1 tangent
   double imp_tol;
   double gfac;  // gamma/(gamma-1)
   double gm1g;  // (gamma-1)/gamma

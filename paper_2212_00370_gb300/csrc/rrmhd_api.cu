@@ -142,6 +142,8 @@ void rrmhd_default_opts(rrmhd_opts* o) {
   o->imp_maxit = 50;
   o->imp_tol = 1e-10;
   o->lanes = 8;
+  o->pvm_k = 3;
+  o->pvm_products = 0;
 }
 
 void rrmhd_destroy(rrmhd_ctx* c) {

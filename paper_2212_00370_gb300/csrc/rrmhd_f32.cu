@@ -10,7 +10,7 @@
 #include "batch.h"
 #include "batch_index.cuh"
 #include "launch_shape.cuh"
-#include "physics_f32.cuh"
+#include "physics_tangent.cuh"
 #include "scheme_f64.cuh"
 
 namespace rr {
@@ -21,14 +21,15 @@ using namespace idx;
 constexpr int kFaceThreads = 128;
 constexpr int kCellThreads = 128;
 
-__device__ __forceinline__ rr32::P32 p32_of(const Params& P) {
-  rr32::P32 q;
+__device__ __forceinline__ rrt::PT<float> p32_of(const Params& P) {
+  rrt::PT<float> q;
   q.gamma = (float)P.gamma;
   q.gfac = (float)P.gfac;
   q.gm1g = (float)P.gm1g;
   q.recon = P.recon;
   q.beta_mode = P.beta_mode;
   q.c2p_maxit = P.c2p_maxit;
+  q.pvm_k = P.pvm_k;
   return q;
 }
 
@@ -54,7 +55,7 @@ static __device__ __noinline__ void face_item_f32(const StageArgs& a, int64_t t)
     q[d] = map_idx(f - 2 + s, I.n[d], I.bc[d]);
     cidx[s] = I.cell_off + ((int64_t)q[2] * I.n[1] + q[1]) * I.n[0] + q[0];
   }
-  const rr32::P32 P = p32_of(a.P);
+  const rrt::PT<float> P = p32_of(a.P);
   const int64_t N = b.ncells;
   float VL[NV], VR[NV];
   {
@@ -62,15 +63,15 @@ static __device__ __noinline__ void face_item_f32(const StageArgs& a, int64_t t)
     load12f(a.Vs, N, cidx[0], w0);
     load12f(a.Vs, N, cidx[1], w1);
     load12f(a.Vs, N, cidx[2], w2);
-    rr32::reconstruct(P.recon, w0, w1, w2, tmp, VL);
+    rrt::reconstruct<float>(P.recon, w0, w1, w2, tmp, VL);
     load12f(a.Vs, N, cidx[3], w0);
-    rr32::reconstruct(P.recon, w1, w2, w0, VR, tmp);
+    rrt::reconstruct<float>(P.recon, w1, w2, w0, VR, tmp);
   }
   const float dxd = (float)I.dx[d];
   const float tauL = (float)(__ldg(a.Us + cidx[1]) * (__ldg(a.kappa + cidx[1]) + __ldg(a.sigma + cidx[1]))) * dxd;
   const float tauR = (float)(__ldg(a.Us + cidx[2]) * (__ldg(a.kappa + cidx[2]) + __ldg(a.sigma + cidx[2]))) * dxd;
   float F[NV];
-  rr32::pvm_flux(P, d, VL, VR, tauL, tauR, F);
+  rrt::pvm_flux<float>(P, d, VL, VR, tauL, tauR, F);
   const int64_t o = g - a.out_base;
 #pragma unroll
   for (int k = 0; k < NV; ++k) a.Fhat32[k * a.fstride + o] = F[k];
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kFaceThreads) k_fallback_faces_f32(StageArgs a
   float vl[NV], vr[NV], F[NV];
   load12f(a.Vs, b.ncells, cl, vl);
   load12f(a.Vs, b.ncells, cr, vr);
-  rr32::llf_flux(p32_of(a.P), d, vl, vr, F);
+  rrt::llf_flux<float>(p32_of(a.P), d, vl, vr, F);
 #pragma unroll
   for (int k = 0; k < NV; ++k) a.Fhat32[k * a.fstride + g] = F[k];
 }

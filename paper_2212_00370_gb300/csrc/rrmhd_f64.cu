@@ -18,6 +18,7 @@
 #include "batch.h"
 #include "batch_index.cuh"
 #include "launch_shape.cuh"
+#include "physics_tangent.cuh"
 #include "scheme_f64.cuh"
 
 namespace rr {
@@ -36,7 +37,64 @@ constexpr int kCellThreads = 128;
 #define RR_CELL_MIN_BLOCKS 1
 #endif
 
-// Face t of the launch's face ranges: stencil, PLM + fallback, PVM-int-8 flux.
+// PVM flux with exact tangent products A w (the FP64 tangent variant): the same
+// reconstruction, central fluxes, con2prim of U_m and beta as pvm_flux, only the
+// A^2 products differ (dual numbers instead of Eq. utilde's flux differences).
+__device__ __forceinline__ int pvm_flux_tangent(const Params& P, int d, const double* VL,
+                                                const double* VR, double tauL, double tauR,
+                                                double* Fhat) {
+  double Um[NV], U0[NV], Ul[NV];
+  double ZL, ZR;
+  {
+    double UL[NV], UR[NV], FL[NV], FR[NV];
+    prim2con(P, VL, UL);
+    prim2con(P, VR, UR);
+    flux(P, d, VL, UL, FL);
+    flux(P, d, VR, UR, FR);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      U0[k] = UR[k] - UL[k];
+      Um[k] = 0.5 * (UL[k] + UR[k]);
+      Fhat[k] = 0.5 * (FL[k] + FR[k]);
+    }
+    ZL = prim_Z(P, VL);
+    ZR = prim_Z(P, VR);
+  }
+  const double Zg = 0.5 * (ZL + ZR);
+  double beta = 1.0;
+  if (P.beta_mode) {
+    double t = tauL > tauR ? tauL : tauR;
+    if (t < 1.0) t = 1.0;
+    beta = 1.0 / t;
+  }
+  int fail = 1;
+  double Vm[NV], Zm = 0.0;
+  if (con2prim(P, Um, Zg, Vm, &Zm) == ST_OK) {
+    rrt::PT<double> Q;
+    Q.gamma = P.gamma;
+    Q.gfac = P.gfac;
+    Q.gm1g = P.gm1g;
+    Q.recon = P.recon;
+    Q.beta_mode = P.beta_mode;
+    Q.c2p_maxit = P.c2p_maxit;
+    Q.pvm_k = P.pvm_k;
+    // W' = Z - D at the root and the residual's derivative there
+    const rrt::C2PIn<double> c = rrt::c2p_in(Um);
+    rrt::C2PPt<double> e;
+    const double xm = Zm - Um[0];
+    rrt::c2p_eval(c, P.gm1g, xm, e);
+    if (e.ok && rrt::pvm_viscosity(Q, d, Um, xm, e.df, U0, Ul)) fail = 0;
+  }
+  if (fail) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) Ul[k] = U0[k];
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) Fhat[k] = Fhat[k] - 0.5 * (beta * Ul[k]);
+  return fail;
+}
+
+// Face t of the launch's face ranges: stencil, PLM + fallback, PVM-int flux.
 static __device__ __noinline__ void face_item(const StageArgs& a, int64_t t) {
   const Batch& b = a.b;
   const int64_t g = lane_face(b, t);
@@ -68,7 +126,10 @@ static __device__ __noinline__ void face_item(const StageArgs& a, int64_t t) {
   const double tauL = (__ldg(a.Us + cidx[1]) * (__ldg(a.kappa + cidx[1]) + __ldg(a.sigma + cidx[1]))) * dxd;
   const double tauR = (__ldg(a.Us + cidx[2]) * (__ldg(a.kappa + cidx[2]) + __ldg(a.sigma + cidx[2]))) * dxd;
   double F[NV];
-  pvm_flux(a.P, d, VL, VR, tauL, tauR, F);
+  if (a.P.pvm_products)
+    pvm_flux_tangent(a.P, d, VL, VR, tauL, tauR, F);
+  else
+    pvm_flux(a.P, d, VL, VR, tauL, tauR, F);
   const int64_t o = g - a.out_base;
 #pragma unroll
   for (int k = 0; k < NV; ++k) a.Fhat[k * a.fstride + o] = F[k];

@@ -48,10 +48,20 @@ __device__ __forceinline__ void reconstruct(int recon, const double* w0, const d
   }
 }
 
-// ------------------------------------------------------------ PVM-int-8
-// p_3(x) = x^2(x^2(x^2(a0 x^2 + a1) + a2) + a3) + a4 (Eq. iterat with k = 3).
+// ------------------------------------------------------------ PVM-int-8 / -16
+// Horner coefficients (in x^2, highest degree first) of the internal
+// approximations of |x| built by Eq. iterat: k = 3 gives p_3 of degree 8 (the
+// printed alpha_0..alpha_4), k = 4 gives p_4 of degree 16 (nine dyadic rationals,
+// p_4 = (2 p_3 - p_3^2 + x^2)/2 expanded).
 __device__ __constant__ const double PVM_ALPHA[5] = {-1.0 / 128.0, 3.0 / 32.0, -23.0 / 64.0,
                                                      31.0 / 32.0, 39.0 / 128.0};
+__device__ __constant__ const double PVM16_ALPHA[9] = {
+    -1.0 / 32768.0, 3.0 / 4096.0,     -59.0 / 8192.0, 169.0 / 4096.0, -2635.0 / 16384.0,
+    1693.0 / 4096.0, -5891.0 / 8192.0, 4807.0 / 4096.0, 8463.0 / 32768.0};
+
+__device__ __forceinline__ double pvm_alpha(int k, int j) {
+  return k == 4 ? PVM16_ALPHA[j] : PVM_ALPHA[j];
+}
 
 // A(U_m)^2 w by two nested flux differences (Sec. 3.2.2 steps 3-5, Eq. utilde).
 // Returns false if a recovery fails.
@@ -73,7 +83,8 @@ __device__ __forceinline__ bool a2_product(const Params& P, int d, const double*
   return true;
 }
 
-// F^ = (F_L + F_R)/2 - beta p_3(A(U_m)) (U_R - U_L)/2  (Eqs. generalflux, beta);
+// F^ = (F_L + F_R)/2 - beta p_k(A(U_m)) (U_R - U_L)/2  (Eqs. generalflux, beta),
+// m = 2^(k-1) A^2 products in Horner order (k = 3: PVM-int-8, 4: PVM-int-16);
 // Q = I (lambda_max = 1 Rusanov) if a recovery inside the viscosity term fails.
 // Returns 1 on that fallback, 0 otherwise.
 __device__ __forceinline__ int pvm_flux(const Params& P, int d, const double* VL,
@@ -116,17 +127,19 @@ __device__ __forceinline__ int pvm_flux(const Params& P, int d, const double* VL
   if (!fail) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) Ul[k] = U0[k];
-    for (int l = 0; l < 4; ++l) {
+    const int m = P.pvm_k == 4 ? 8 : 4;
+    for (int l = 0; l < m; ++l) {
       double Y[NV];
       if (!a2_product(P, d, Um, Fm, Zm, Ul, Y)) {
         fail = 1;
         break;
       }
       if (l == 0) {
+        const double a0 = pvm_alpha(P.pvm_k, 0), a1 = pvm_alpha(P.pvm_k, 1);
 #pragma unroll
-        for (int k = 0; k < NV; ++k) Ul[k] = PVM_ALPHA[0] * Y[k] + PVM_ALPHA[1] * U0[k];
+        for (int k = 0; k < NV; ++k) Ul[k] = a0 * Y[k] + a1 * U0[k];
       } else {
-        const double al = PVM_ALPHA[l + 1];
+        const double al = pvm_alpha(P.pvm_k, l + 1);
 #pragma unroll
         for (int k = 0; k < NV; ++k) Ul[k] = Y[k] + al * U0[k];
       }

@@ -31,7 +31,8 @@ class rrmhd_opts(C.Structure):
     _fields_ = [("gamma", C.c_double), ("a_rad", C.c_double), ("cfl", C.c_double),
                 ("pvm_eps", C.c_double), ("recon", C.c_int), ("beta_mode", C.c_int),
                 ("precision", C.c_int), ("c2p_maxit", C.c_int), ("imp_maxit", C.c_int),
-                ("imp_tol", C.c_double), ("lanes", C.c_int)]
+                ("imp_tol", C.c_double), ("lanes", C.c_int), ("pvm_k", C.c_int),
+                ("pvm_products", C.c_int)]
 
 
 class rrmhd_tuning(C.Structure):
@@ -174,6 +175,8 @@ def make_opts(**kw):
             v = PRECISION[v]
         if k == "beta":
             k, v = "beta_mode", int(bool(v))
+        if k == "pvm_products" and isinstance(v, str):
+            v = {"fd": 0, "tangent": 1}[v]
         setattr(o, k, v)
     return o
 

@@ -39,6 +39,42 @@ def test_p3_coefficients_and_bounds():
     assert horner[1000] == pytest.approx(39 / 128)
 
 
+def test_pvm_coefficients_follow_the_recurrence():
+    """Eq. iterat in exact rational arithmetic (fractions) gives the coefficients of
+    p_k in y = x^2; the oracle's table equals them, k = 3 equals the printed alpha,
+    and every p_k is an internal approximation: p_k(x) >= |x|, p_k(+-1) = 1."""
+    from fractions import Fraction
+
+    assert list(O.pvm_coefficients(3)) == ALPHA_PAPER
+    c = [Fraction(1)]                       # ascending powers of y
+    for k in range(1, 5):
+        sq = [Fraction(0)] * (2 * len(c) - 1)
+        for a, ca in enumerate(c):
+            for b, cb in enumerate(c):
+                sq[a + b] += ca * cb
+        n = max(len(sq), 2)
+        c = [(2 * (c[a] if a < len(c) else 0) - (sq[a] if a < len(sq) else 0) + (1 if a == 1 else 0)) / 2
+             for a in range(n)]
+        exact = [float(v) for v in reversed(c)]
+        assert list(O.pvm_coefficients(k)) == exact, k
+        x = np.linspace(-1, 1, 4001)
+        p = np.zeros_like(x)
+        for a in exact:
+            p = p * x * x + a
+        assert np.all(p >= np.abs(x) - 1e-14)
+        assert p[0] == pytest.approx(1.0, abs=1e-14) and p[-1] == pytest.approx(1.0, abs=1e-14)
+    # PVM-int-16 is the closer approximation of |x|
+    x = np.linspace(-1, 1, 4001)
+    err = []
+    for k in (3, 4):
+        p = np.zeros_like(x)
+        for a in O.pvm_coefficients(k):
+            p = p * x * x + a
+        err.append(np.abs(p - np.abs(x)).max())
+    assert err[1] < err[0]
+    assert len(O.pvm_coefficients(4)) == 9
+
+
 def test_limiters():
     for r in ("minmod", "mc", "vanleer"):
         assert O.limiter(r, 1.0, -2.0) == 0.0
@@ -86,10 +122,12 @@ def _jacobian(Um, d, P, Zg):
     return A
 
 
-@pytest.mark.parametrize("seed", range(6))
-def test_pvm_viscosity_equals_p3_of_assembled_jacobian(seed):
+@pytest.mark.parametrize("seed,k", [(s, 3) for s in range(6)] + [(s, 4) for s in range(3)])
+def test_pvm_viscosity_equals_p3_of_assembled_jacobian(seed, k):
+    """U_m = p_k(A) U_0 with A assembled column by column; k = 3 (PVM-int-8) and
+    k = 4 (PVM-int-16, eight A^2 products)."""
     rng = np.random.default_rng(seed)
-    P = O.Params(gamma=4 / 3)
+    P = O.Params(gamma=4 / 3, pvm_k=k)
     d = seed % 3
     n = rng.normal(size=3)
     n /= np.linalg.norm(n)
@@ -111,7 +149,7 @@ def test_pvm_viscosity_equals_p3_of_assembled_jacobian(seed):
     assert np.all(np.abs(ev.real) <= 1 + 1e-6) and np.all(np.abs(ev.imag) < 1e-6)
     Q = np.eye(12)
     A2 = A @ A
-    for _ in range(3):
+    for _ in range(k):
         Q = 0.5 * (2 * Q - Q @ Q + A2)
     U0 = UR - UL
     ref = Q @ U0
