@@ -32,7 +32,8 @@ class _Params(C.Structure):
     _fields_ = [
         ("gamma", C.c_double), ("a_rad", C.c_double), ("cfl", C.c_double),
         ("pvm_eps", C.c_double), ("recon", C.c_int), ("beta_mode", C.c_int),
-        ("imp_mode", C.c_int), ("pvm_k", C.c_int), ("c2p_maxit", C.c_int), ("imp_maxit", C.c_int),
+        ("imp_mode", C.c_int), ("pvm_k", C.c_int), ("solver", C.c_int), ("c2p_maxit", C.c_int),
+        ("imp_maxit", C.c_int),
         ("imp_tol", C.c_double), ("gfac", C.c_double), ("gm1g", C.c_double),
     ]
 
@@ -63,10 +64,12 @@ class Params:
     imp_maxit: int = 50
     imp_tol: float = 1e-10
     pvm_k: int = 3          # PVM-int-2^k: 3 is the paper's PVM-int-8, 4 is PVM-int-16
+    solver: str = "pvm"     # "pvm" (Sec. 3.2.2) or "radhll" (Sec. 3.2.1)
 
     def struct(self):
         p = _Params(self.gamma, self.a_rad, self.cfl, self.pvm_eps, RECON[self.recon],
                     1 if self.beta else 0, 0 if self.implicit == "newton" else 1, self.pvm_k,
+                    {"pvm": 0, "radhll": 1}[self.solver],
                     self.c2p_maxit, self.imp_maxit, self.imp_tol, 0.0, 0.0)
         lib().or_params_init(C.byref(p))
         return p
@@ -121,6 +124,9 @@ def lib():
                                         C.c_double, C.c_double, dp, dp, dp, dp]),
             "or_solve4": (C.c_int, [dp, dp, dp]),
             "or_llf_flux": (None, [P, C.c_int, dp, dp, dp]),
+            "or_radhll_flux": (None, [P, C.c_int, dp, dp, C.c_double, C.c_double, dp]),
+            "or_mhd_speeds": (None, [P, C.c_int, dp, dp, dp]),
+            "or_rad_speeds": (None, [C.c_int, dp, dp, dp]),
             "or_grid_dt": (C.c_double, [P, G, dp]),
             "or_grid_face_flux": (C.c_int, [P, G, C.c_int, dp, dp, dp, dp, dp, S]),
             "or_grid_stage": (C.c_int, [P, G, C.c_int, C.c_double, dp, dp, dp, dp, dp, dp, dp,
@@ -292,6 +298,29 @@ def llf_flux(VL, VR, d, P):
     F = np.empty(12)
     lib().or_llf_flux(C.byref(P.struct()), d, _d(VL), _d(VR), _d(F))
     return F
+
+
+def radhll_flux(VL, VR, tauL, tauR, d, P):
+    """Radiative HLL flux at one face (Sec. 3.2.1)."""
+    VL = np.ascontiguousarray(VL, dtype=np.float64)
+    VR = np.ascontiguousarray(VR, dtype=np.float64)
+    F = np.empty(12)
+    lib().or_radhll_flux(C.byref(P.struct()), d, _d(VL), _d(VR), float(tauL), float(tauR), _d(F))
+    return F
+
+
+def mhd_speeds(V, d, P):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    lm, lp = C.c_double(), C.c_double()
+    lib().or_mhd_speeds(C.byref(P.struct()), d, _d(V), C.byref(lm), C.byref(lp))
+    return lm.value, lp.value
+
+
+def rad_speeds(V, d):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    l1, l3 = C.c_double(), C.c_double()
+    lib().or_rad_speeds(d, _d(V), C.byref(l1), C.byref(l3))
+    return l1.value, l3.value
 
 
 def solve4(A, b):

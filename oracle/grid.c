@@ -92,7 +92,10 @@ int or_grid_face_flux(const or_params* P, const or_grid* g, int dir, const doubl
                 or_reconstruct(P, w[1], w[2], w[3], VR, Vp, 0); /* cell f:   left face  */
                 double tauL = (U[cidx[1]] * (kappa[cidx[1]] + sigma[cidx[1]])) * g->dx[dir];
                 double tauR = (U[cidx[2]] * (kappa[cidx[2]] + sigma[cidx[2]])) * g->dx[dir];
-                nfb += or_pvm_flux(P, dir, VL, VR, tauL, tauR, F, 0, st);
+                if (P->solver == OR_SOLVER_RADHLL)
+                    or_radhll_flux(P, dir, VL, VR, tauL, tauR, F);
+                else
+                    nfb += or_pvm_flux(P, dir, VL, VR, tauL, tauR, F, 0, st);
                 int64_t fi = ((int64_t)k * m[1] + j) * m[0] + i;
                 for (int q = 0; q < 12; q++) Fhat[q * NF + fi] = F[q];
             }

@@ -32,6 +32,7 @@ extern "C" {
 enum { OR_RECON_GODUNOV = 0, OR_RECON_MINMOD = 1, OR_RECON_MC = 2, OR_RECON_VANLEER = 3 };
 enum { OR_BC_OUTFLOW = 0, OR_BC_PERIODIC = 1 };
 enum { OR_IMP_NEWTON = 0, OR_IMP_PICARD = 1 };
+enum { OR_SOLVER_PVM = 0, OR_SOLVER_RADHLL = 1 };
 
 /* status codes (per call) */
 enum {
@@ -50,6 +51,7 @@ typedef struct {
     int    beta_mode;  /* 1: beta = min(1/tau_L, 1/tau_R, 1) (Eq. beta); 0: beta=1  */
     int    imp_mode;   /* OR_IMP_NEWTON (default) or OR_IMP_PICARD (paper's C matrix) */
     int    pvm_k;      /* PVM-int-n with n = 2^k (Eq. iterat): 3 (PVM-int-8), 4 (-16) */
+    int    solver;     /* OR_SOLVER_PVM (Sec. 3.2.2) or OR_SOLVER_RADHLL (Sec. 3.2.1)  */
     int    c2p_maxit;  /* Newton iterations allowed in con2prim                    */
     int    imp_maxit;  /* outer iterations allowed in the implicit solve           */
     double imp_tol;    /* implicit convergence: max|dX| <= imp_tol * E_r           */
@@ -89,6 +91,10 @@ int    or_pvm_flux(const or_params* P, int dir, const double VL[12], const doubl
                    double tauL, double tauR, double Fhat[12], double U4[12], or_stats* st);
 void   or_llf_flux(const or_params* P, int dir, const double VL[12], const double VR[12],
                    double Fhat[12]);
+void   or_radhll_flux(const or_params* P, int dir, const double VL[12], const double VR[12],
+                      double tauL, double tauR, double Fhat[12]);
+void   or_mhd_speeds(const or_params* P, int dir, const double V[12], double* lm, double* lp);
+void   or_rad_speeds(int dir, const double V[12], double* l1, double* l3);
 
 /* ---- implicit step (implicit.c) ---- */
 int  or_implicit(const or_params* P, double kappa, double sigma, double hdt,

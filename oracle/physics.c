@@ -261,7 +261,9 @@ int or_con2prim(const or_params* P, const double U[12], double Zguess,
  *   lambda = [v^d (1 - a^2) +- sqrt(a^2 (1 - v^2)(1 - v^2 a^2 - (v^d)^2 (1 - a^2)))]/(1 - v^2 a^2).
  * Radiation: lambda_r1, lambda_r3 of Eqs. lam1-lam3 with theta the angle between F_r
  * and the sweep direction. */
-double or_signal_speed(const or_params* P, int d, const double V[12])
+/* Signed fast-magnetosonic speed estimates lm <= lp of one state along d (the
+ * Del Zanna et al. 2007 expressions above). */
+void or_mhd_speeds(const or_params* P, int d, const double V[12], double* lm, double* lp)
 {
     aux_t a;
     aux_of(P, V, &a);
@@ -273,10 +275,14 @@ double or_signal_speed(const or_params* P, int d, const double V[12])
     double disc = (a2 * (1.0 - a.v2)) * (den - (vd * vd) * (1.0 - a2));
     if (disc < 0.0) disc = 0.0;
     double sq = sqrt(disc);
-    double lp = (vd * (1.0 - a2) + sq) / den;
-    double lm = (vd * (1.0 - a2) - sq) / den;
-    double lf = fabs(lp) > fabs(lm) ? fabs(lp) : fabs(lm);
+    *lp = (vd * (1.0 - a2) + sq) / den;
+    *lm = (vd * (1.0 - a2) - sq) / den;
+}
 
+/* Outer radiation eigenvalues lambda_r1 <= lambda_r3 of Eqs. lam1-lam3, theta the
+ * angle between F_r and the direction d (cos theta = 0 when F_r = 0). */
+void or_rad_speeds(int d, const double V[12], double* l1, double* l3)
+{
     double E = V[8];
     double F2 = (V[9] * V[9] + V[10] * V[10]) + V[11] * V[11];
     double Fn = sqrt(F2);
@@ -288,8 +294,16 @@ double or_signal_speed(const or_params* P, int d, const double V[12])
     double arg = (2.0 / 3.0) * ((4.0 - 3.0 * f2) - s) + (2.0 * (cth * cth)) * ((2.0 - f2) - s);
     if (arg < 0.0) arg = 0.0;
     double zeta = sqrt(arg);
-    double l1 = (f * cth - zeta) / s;
-    double l3 = (f * cth + zeta) / s;
+    *l1 = (f * cth - zeta) / s;
+    *l3 = (f * cth + zeta) / s;
+}
+
+double or_signal_speed(const or_params* P, int d, const double V[12])
+{
+    double lm, lp, l1, l3;
+    or_mhd_speeds(P, d, V, &lm, &lp);
+    double lf = fabs(lp) > fabs(lm) ? fabs(lp) : fabs(lm);
+    or_rad_speeds(d, V, &l1, &l3);
     double lr = fabs(l1) > fabs(l3) ? fabs(l1) : fabs(l3);
 
     double lam = lf > lr ? lf : lr;

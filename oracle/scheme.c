@@ -192,6 +192,57 @@ void or_llf_flux(const or_params* P, int dir, const double VL[12], const double 
     for (int k = 0; k < 12; k++) Fhat[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * (UR[k] - UL[k]);
 }
 
+/* HLL flux (Sec. 3.2.1) of components [k0, k1) with wave speeds sL <= sR:
+ *   F_L if sL > 0;  F_R if sR < 0;  else (sR F_L - sL F_R + sR sL (U_R - U_L))/(sR - sL).
+ * A degenerate fan (sR == sL == 0) takes the central flux. */
+static void hll_block(int k0, int k1, double sL, double sR, const double* UL, const double* UR,
+                      const double* FL, const double* FR, double* F)
+{
+    for (int k = k0; k < k1; k++) {
+        if (sL > 0.0)
+            F[k] = FL[k];
+        else if (sR < 0.0)
+            F[k] = FR[k];
+        else if (sR > sL)
+            F[k] = ((sR * FL[k] - sL * FR[k]) + (sR * sL) * (UR[k] - UL[k])) / (sR - sL);
+        else
+            F[k] = 0.5 * (FL[k] + FR[k]);
+    }
+}
+
+/* Radiative HLL flux (Sec. 3.2.1): the magnetofluid block (D, S, tau, B) with the
+ * fast-magnetosonic speeds of the two reconstructed states, sL = min(lm_L, lm_R),
+ * sR = max(lp_L, lp_R); the radiation block (E_r, F_r) with the outer radiation
+ * eigenvalues rL = min(l1_L, l1_R), rR = max(l3_L, l3_R), limited in optically
+ * thick cells by Eq. limits, rL >= -4/(3 tau), rR <= 4/(3 tau), with tau the
+ * larger optical depth of the two cells next to the face (beta_mode = 1). */
+void or_radhll_flux(const or_params* P, int dir, const double VL[12], const double VR[12],
+                    double tauL, double tauR, double Fhat[12])
+{
+    double UL[12], UR[12], FL[12], FR[12];
+    or_prim2con(P, VL, UL);
+    or_prim2con(P, VR, UR);
+    or_flux(P, dir, VL, UL, FL);
+    or_flux(P, dir, VR, UR, FR);
+    double lmL, lpL, lmR, lpR, r1L, r3L, r1R, r3R;
+    or_mhd_speeds(P, dir, VL, &lmL, &lpL);
+    or_mhd_speeds(P, dir, VR, &lmR, &lpR);
+    or_rad_speeds(dir, VL, &r1L, &r3L);
+    or_rad_speeds(dir, VR, &r1R, &r3R);
+    double sL = lmL < lmR ? lmL : lmR;
+    double sR = lpL > lpR ? lpL : lpR;
+    double rL = r1L < r1R ? r1L : r1R;
+    double rR = r3L > r3R ? r3L : r3R;
+    double t = tauL > tauR ? tauL : tauR;
+    if (P->beta_mode && t > 0.0) {
+        double lim = 4.0 / (3.0 * t);
+        if (rL < -lim) rL = -lim;
+        if (rR > lim) rR = lim;
+    }
+    hll_block(0, 8, sL, sR, UL, UR, FL, FR, Fhat);
+    hll_block(8, 12, rL, rR, UL, UR, FL, FR, Fhat);
+}
+
 void or_pvm_flux_n(const or_params* P, int dir, int64_t n, const double* VL, const double* VR,
                    const double* tauL, const double* tauR, double* Fhat, double* U4,
                    int32_t* status, or_stats* st)

@@ -274,9 +274,9 @@ def test_free_streaming_front_moves_at_c():
     assert np.abs(V[9] - V[8]).max() <= 1e-6 * V[8].max()
 
 
-def _periodic_conservation(ndim, n, seed, steps=4):
+def _periodic_conservation(ndim, n, seed, steps=4, solver="pvm"):
     rng = np.random.default_rng(seed)
-    P = O.Params(gamma=4 / 3, cfl=0.4, a_rad=1.0)
+    P = O.Params(gamma=4 / 3, cfl=0.4, a_rad=1.0, solver=solver)
     shape = (n,) * ndim
     N = n ** ndim
     xs = np.meshgrid(*[(np.arange(n) + 0.5) / n for _ in range(ndim)], indexing="ij")
