@@ -4,9 +4,13 @@
 Workload (default): a batch of 4096 independent 1D RRMHD Riemann problems from
 seed 2212003701 (grid sizes U{128..2048}, log-uniform densities, pressures,
 radiation energies and opacities, Lorentz factors up to 10, gamma 4/3), all
-advanced together, FP64.  One "step" is one IMEX-RK3 step of every live
-instance (3 stages x {PLM + PVM-int-8 fluxes, flux difference + RK, implicit
+advanced together.  One "step" is one IMEX-RK3 step of every live instance
+(3 stages x {PLM + PVM-int-8 fluxes, flux difference + RK, implicit
 radiation-matter solve}); a zone-update is one cell advanced by one step.
+The headline is the FP32-bulk form; the FP64 form (and FP64 with tangent
+products) are measured beside it.  Launch shapes are autotuned before timing
+(untimed, state restored).  A serving sample of the C4 arrival process (continuous
+batching, time to solution) and the CPU oracle are measured too.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -36,13 +40,14 @@ sys.path.insert(0, ROOT)
 # sm__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum) per cell of ONE launch
 # of each kernel in the steady state of this workload (stage 1 of the 4th step),
 # measured with ncu on a 2048-instance sample of the same distribution
-# (profiles/c1_fp64_k_cells_k_faces.md).
+# (profiles/c1_k_cells_k_faces_counters.md).
 FP64_INST_PER_ZONE = {"fp64": {"faces": 5640.0, "cells": 5439.0},
-                      "fp32_bulk": {"faces": None, "cells": 4299.0},
-                      "fp64_tangent": {"faces": None, "cells": 5439.0}}
+                      "fp32_bulk": {"faces": None, "cells": 4536.0},
+                      "fp64_tangent": {"faces": 5249.0, "cells": 5278.0}}
 # DRAM bytes per cell of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
-TRAFFIC_PER_CELL = {"fp64": {"faces": 240.0, "cells": 1033.0},
-                    "fp32_bulk": {"faces": 167.0, "cells": 935.0}, "fp64_tangent": {}}
+TRAFFIC_PER_CELL = {"fp64": {"faces": 248.0, "cells": 1059.0},
+                    "fp32_bulk": {"faces": 166.0, "cells": 962.0},
+                    "fp64_tangent": {"faces": 237.0, "cells": 1061.0}}
 # Nominal FP64 rate of GB300: 1.25 TFLOP/s = 6.25e11 FP64-pipe instructions/s
 # (2 per SM per clock on 152 SMs at 2.07 GHz); no MEASURED_PEAKS entry exists for FP64.
 FP64_PEAK_INST = 6.25e11

@@ -53,6 +53,7 @@ typedef enum {
 enum { RRMHD_RECON_GODUNOV = 0, RRMHD_RECON_MINMOD = 1, RRMHD_RECON_MC = 2, RRMHD_RECON_VANLEER = 3 };
 enum { RRMHD_BC_OUTFLOW = 0, RRMHD_BC_PERIODIC = 1 };
 enum { RRMHD_FP64 = 0, RRMHD_FP32_BULK = 1 };
+enum { RRMHD_SOLVER_PVM = 0, RRMHD_SOLVER_RADHLL = 1 };
 
 /* One instance's grid.  Unused directions: n = 1, dx = 1.  bc applies to both
  * sides of a direction: outflow copies the edge cell into the two ghost layers
@@ -88,6 +89,11 @@ typedef struct {
                           the root of con2prim differentiated by the implicit-function
                           theorem: no Newton iteration per product.  The FP32-bulk form
                           always uses tangent products (eps is below FP32 resolution). */
+    int    solver;     /* RRMHD_SOLVER_PVM (Sec. 3.2.2, default) or RRMHD_SOLVER_RADHLL: the
+                          radiative HLL of Sec. 3.2.1, HLL per block with the fast-
+                          magnetosonic speeds for the magnetofluid and lambda_r1/lambda_r3
+                          (Eqs. lam1-lam3) for the radiation, the latter capped at
+                          4/(3 tau) (Eq. limits) when beta_mode = 1                      */
 } rrmhd_opts;
 
 typedef struct rrmhd_ctx rrmhd_ctx;

@@ -30,6 +30,7 @@ inline Params make_params(const rrmhd_opts& o) {
   P.imp_tol = o.imp_tol;
   P.pvm_k = o.pvm_k;
   P.pvm_products = o.pvm_products;
+  P.solver = o.solver;
   P.gfac = o.gamma / (o.gamma - 1.0);
   P.gm1g = (o.gamma - 1.0) / o.gamma;
   return P;
@@ -39,7 +40,8 @@ inline bool opts_ok(const rrmhd_opts& o) {
   return o.gamma > 1.0 && o.a_rad >= 0.0 && o.cfl > 0.0 && o.pvm_eps > 0.0 && o.recon >= 0 &&
          o.recon <= 3 && o.c2p_maxit >= 1 && o.imp_maxit >= 1 && o.imp_tol > 0.0 &&
          (o.precision == RRMHD_FP64 || o.precision == RRMHD_FP32_BULK) && o.lanes >= 1 &&
-         (o.pvm_k == 3 || o.pvm_k == 4) && (o.pvm_products == 0 || o.pvm_products == 1);
+         (o.pvm_k == 3 || o.pvm_k == 4) && (o.pvm_products == 0 || o.pvm_products == 1) &&
+         (o.solver == RRMHD_SOLVER_PVM || o.solver == RRMHD_SOLVER_RADHLL);
 }
 
 inline bool grid_ok(const rrmhd_grid& g, std::string& why) {

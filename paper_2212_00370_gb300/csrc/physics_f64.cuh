@@ -33,6 +33,7 @@ struct Params {
   int recon, beta_mode, c2p_maxit, imp_maxit;
   int pvm_k;  // PVM-int-2^k: 3 (PVM-int-8) or 4 (PVM-int-16)
   int pvm_products;  // FP64 A w products: 0 nested flux differences (Eq. utilde), 1 tangent
+  int solver;        // 0 PVM-int (Sec. 3.2.2), 1 radiative HLL (Sec. 3.2.1)
   double imp_tol;
   double gfac;  // gamma/(gamma-1)
   double gm1g;  // (gamma-1)/gamma
@@ -260,7 +261,9 @@ static __device__ __noinline__ int con2prim(const Params& P, const double* U, do
 // ------------------------------------------------------------- signal speed
 // max |lambda| along d, capped at 1: fast-magnetosonic estimate (Del Zanna et
 // al. 2007) and the radiation eigenvalues lambda_r1, lambda_r3 (Eqs. lam1-lam3).
-__device__ __forceinline__ double signal_speed(const Params& P, int d, const double* V) {
+// Signed fast-magnetosonic speed estimates lm <= lp along d (Del Zanna et al. 2007).
+__device__ __forceinline__ void mhd_speeds(const Params& P, int d, const double* V, double& lm,
+                                           double& lp) {
   Aux a;
   aux_of(P, V, a);
   const double cs2 = (P.gamma * V[4]) / a.rhoh;
@@ -271,10 +274,12 @@ __device__ __forceinline__ double signal_speed(const Params& P, int d, const dou
   double disc = (a2 * (1.0 - a.v2)) * (den - (vd * vd) * (1.0 - a2));
   if (disc < 0.0) disc = 0.0;
   const double sq = sqrt(disc);
-  const double lp = (vd * (1.0 - a2) + sq) / den;
-  const double lm = (vd * (1.0 - a2) - sq) / den;
-  const double lf = fabs(lp) > fabs(lm) ? fabs(lp) : fabs(lm);
+  lp = (vd * (1.0 - a2) + sq) / den;
+  lm = (vd * (1.0 - a2) - sq) / den;
+}
 
+// Outer radiation eigenvalues l1 <= l3 (Eqs. lam1-lam3), theta between F_r and d.
+__device__ __forceinline__ void rad_speeds(int d, const double* V, double& l1, double& l3) {
   const double E = V[8];
   const double F2 = (V[9] * V[9] + V[10] * V[10]) + V[11] * V[11];
   const double Fn = sqrt(F2);
@@ -286,8 +291,15 @@ __device__ __forceinline__ double signal_speed(const Params& P, int d, const dou
   double arg = (2.0 / 3.0) * ((4.0 - 3.0 * f2) - s) + (2.0 * (cth * cth)) * ((2.0 - f2) - s);
   if (arg < 0.0) arg = 0.0;
   const double zeta = sqrt(arg);
-  const double l1 = (f * cth - zeta) / s;
-  const double l3 = (f * cth + zeta) / s;
+  l1 = (f * cth - zeta) / s;
+  l3 = (f * cth + zeta) / s;
+}
+
+__device__ __forceinline__ double signal_speed(const Params& P, int d, const double* V) {
+  double lm, lp, l1, l3;
+  mhd_speeds(P, d, V, lm, lp);
+  const double lf = fabs(lp) > fabs(lm) ? fabs(lp) : fabs(lm);
+  rad_speeds(d, V, l1, l3);
   const double lr = fabs(l1) > fabs(l3) ? fabs(l1) : fabs(l3);
   double lam = lf > lr ? lf : lr;
   if (lam > 1.0) lam = 1.0;

@@ -406,6 +406,75 @@ __device__ __forceinline__ int pvm_flux(const PT<S>& P, int d, const S* VL, cons
   return fail;
 }
 
+// Signed fast-magnetosonic speed estimates (Del Zanna et al. 2007) and the outer
+// radiation eigenvalues (Eqs. lam1-lam3) of one state along d.
+template <class S>
+__device__ __forceinline__ void mhd_speeds(const PT<S>& P, int d, const S* V, S& lm, S& lp) {
+  Aux<S> a;
+  aux_of(P, V, a);
+  const S cs2 = (P.gamma * V[4]) / a.rhoh;
+  const S ca2 = a.bsq / (a.rhoh + a.bsq);
+  const S a2 = (cs2 + ca2) - cs2 * ca2;
+  const S vd = V[1 + d];
+  const S den = S(1) - a.v2 * a2;
+  S disc = (a2 * (S(1) - a.v2)) * (den - (vd * vd) * (S(1) - a2));
+  if (disc < S(0)) disc = S(0);
+  const S sq = tsqrt(disc);
+  lp = (vd * (S(1) - a2) + sq) / den;
+  lm = (vd * (S(1) - a2) - sq) / den;
+}
+
+template <class S>
+__device__ __forceinline__ void rad_speeds(int d, const S* V, S& l1, S& l3) {
+  const S E = V[8];
+  const S Fn = tsqrt(V[9] * V[9] + V[10] * V[10] + V[11] * V[11]);
+  S f = Fn / E;
+  if (f > S(1)) f = S(1);
+  const S cth = (Fn > S(0)) ? V[9 + d] / Fn : S(0);
+  const S f2 = f * f;
+  const S s = tsqrt(S(4) - S(3) * f2);
+  S arg = S(2.0 / 3.0) * ((S(4) - S(3) * f2) - s) + (S(2) * (cth * cth)) * ((S(2) - f2) - s);
+  if (arg < S(0)) arg = S(0);
+  const S zeta = tsqrt(arg);
+  l1 = (f * cth - zeta) / s;
+  l3 = (f * cth + zeta) / s;
+}
+
+// Radiative HLL (Sec. 3.2.1), as in the FP64 path.
+template <class S>
+__device__ __forceinline__ void radhll_flux(const PT<S>& P, int d, const S* VL, const S* VR, S tauL,
+                                            S tauR, S* Fhat) {
+  S UL[NV], UR[NV], FL[NV], FR[NV];
+  prim2con(P, VL, UL);
+  prim2con(P, VR, UR);
+  flux(P, d, VL, UL, FL);
+  flux(P, d, VR, UR, FR);
+  S lmL, lpL, lmR, lpR, r1L, r3L, r1R, r3R;
+  mhd_speeds(P, d, VL, lmL, lpL);
+  mhd_speeds(P, d, VR, lmR, lpR);
+  rad_speeds(d, VL, r1L, r3L);
+  rad_speeds(d, VR, r1R, r3R);
+  const S sL = tmin(lmL, lmR), sR = tmax(lpL, lpR);
+  S rL = tmin(r1L, r1R), rR = tmax(r3L, r3R);
+  const S t = tmax(tauL, tauR);
+  if (P.beta_mode && t > S(0)) {
+    const S lim = S(4) / (S(3) * t);
+    rL = tmax(rL, -lim);
+    rR = tmin(rR, lim);
+  }
+  for (int k = 0; k < NV; ++k) {
+    const S lo = k < 8 ? sL : rL, hi = k < 8 ? sR : rR;
+    if (lo > S(0))
+      Fhat[k] = FL[k];
+    else if (hi < S(0))
+      Fhat[k] = FR[k];
+    else if (hi > lo)
+      Fhat[k] = ((hi * FL[k] - lo * FR[k]) + (hi * lo) * (UR[k] - UL[k])) / (hi - lo);
+    else
+      Fhat[k] = S(0.5) * (FL[k] + FR[k]);
+  }
+}
+
 template <class S>
 __device__ __forceinline__ void llf_flux(const PT<S>& P, int d, const S* VL, const S* VR, S* Fhat) {
   S UL[NV], UR[NV], FL[NV], FR[NV];

@@ -144,6 +144,7 @@ void rrmhd_default_opts(rrmhd_opts* o) {
   o->lanes = 8;
   o->pvm_k = 3;
   o->pvm_products = 0;
+  o->solver = RRMHD_SOLVER_PVM;
 }
 
 void rrmhd_destroy(rrmhd_ctx* c) {

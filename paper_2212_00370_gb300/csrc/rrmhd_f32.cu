@@ -71,7 +71,10 @@ static __device__ __noinline__ void face_item_f32(const StageArgs& a, int64_t t)
   const float tauL = (float)(__ldg(a.Us + cidx[1]) * (__ldg(a.kappa + cidx[1]) + __ldg(a.sigma + cidx[1]))) * dxd;
   const float tauR = (float)(__ldg(a.Us + cidx[2]) * (__ldg(a.kappa + cidx[2]) + __ldg(a.sigma + cidx[2]))) * dxd;
   float F[NV];
-  rrt::pvm_flux<float>(P, d, VL, VR, tauL, tauR, F);
+  if (a.P.solver == 1)
+    rrt::radhll_flux<float>(P, d, VL, VR, tauL, tauR, F);
+  else
+    rrt::pvm_flux<float>(P, d, VL, VR, tauL, tauR, F);
   const int64_t o = g - a.out_base;
 #pragma unroll
   for (int k = 0; k < NV; ++k) a.Fhat32[k * a.fstride + o] = F[k];

@@ -126,7 +126,9 @@ static __device__ __noinline__ void face_item(const StageArgs& a, int64_t t) {
   const double tauL = (__ldg(a.Us + cidx[1]) * (__ldg(a.kappa + cidx[1]) + __ldg(a.sigma + cidx[1]))) * dxd;
   const double tauR = (__ldg(a.Us + cidx[2]) * (__ldg(a.kappa + cidx[2]) + __ldg(a.sigma + cidx[2]))) * dxd;
   double F[NV];
-  if (a.P.pvm_products)
+  if (a.P.solver == 1)
+    radhll_flux(a.P, d, VL, VR, tauL, tauR, F);
+  else if (a.P.pvm_products)
     pvm_flux_tangent(a.P, d, VL, VR, tauL, tauR, F);
   else
     pvm_flux(a.P, d, VL, VR, tauL, tauR, F);

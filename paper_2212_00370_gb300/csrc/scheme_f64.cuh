@@ -154,6 +154,53 @@ __device__ __forceinline__ int pvm_flux(const Params& P, int d, const double* VL
   return fail;
 }
 
+// HLL flux of components [k0, k1) with wave speeds sL <= sR (Sec. 3.2.1); a
+// degenerate fan (sR == sL == 0) takes the central flux.
+__device__ __forceinline__ void hll_block(int k0, int k1, double sL, double sR, const double* UL,
+                                          const double* UR, const double* FL, const double* FR,
+                                          double* F) {
+  for (int k = k0; k < k1; ++k) {
+    if (sL > 0.0)
+      F[k] = FL[k];
+    else if (sR < 0.0)
+      F[k] = FR[k];
+    else if (sR > sL)
+      F[k] = ((sR * FL[k] - sL * FR[k]) + (sR * sL) * (UR[k] - UL[k])) / (sR - sL);
+    else
+      F[k] = 0.5 * (FL[k] + FR[k]);
+  }
+}
+
+// Radiative HLL (Sec. 3.2.1): magnetofluid block with the fast-magnetosonic speeds
+// of the two states, radiation block with lambda_r1/lambda_r3, limited by Eq. limits
+// to 4/(3 tau) (tau the larger of the two cells' optical depths) when beta_mode.
+__device__ __forceinline__ void radhll_flux(const Params& P, int d, const double* VL,
+                                            const double* VR, double tauL, double tauR,
+                                            double* Fhat) {
+  double UL[NV], UR[NV], FL[NV], FR[NV];
+  prim2con(P, VL, UL);
+  prim2con(P, VR, UR);
+  flux(P, d, VL, UL, FL);
+  flux(P, d, VR, UR, FR);
+  double lmL, lpL, lmR, lpR, r1L, r3L, r1R, r3R;
+  mhd_speeds(P, d, VL, lmL, lpL);
+  mhd_speeds(P, d, VR, lmR, lpR);
+  rad_speeds(d, VL, r1L, r3L);
+  rad_speeds(d, VR, r1R, r3R);
+  const double sL = lmL < lmR ? lmL : lmR;
+  const double sR = lpL > lpR ? lpL : lpR;
+  double rL = r1L < r1R ? r1L : r1R;
+  double rR = r3L > r3R ? r3L : r3R;
+  const double t = tauL > tauR ? tauL : tauR;
+  if (P.beta_mode && t > 0.0) {
+    const double lim = 4.0 / (3.0 * t);
+    if (rL < -lim) rL = -lim;
+    if (rR > lim) rR = lim;
+  }
+  hll_block(0, 8, sL, sR, UL, UR, FL, FR, Fhat);
+  hll_block(8, 12, rL, rR, UL, UR, FL, FR, Fhat);
+}
+
 // First-order Rusanov flux with lambda_max = 1 (Q = I in Eq. generalflux) from
 // the cell-centre states; used only by the admissibility fallback.
 __device__ __forceinline__ void llf_flux(const Params& P, int d, const double* VL,

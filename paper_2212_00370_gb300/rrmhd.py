@@ -32,7 +32,7 @@ class rrmhd_opts(C.Structure):
                 ("pvm_eps", C.c_double), ("recon", C.c_int), ("beta_mode", C.c_int),
                 ("precision", C.c_int), ("c2p_maxit", C.c_int), ("imp_maxit", C.c_int),
                 ("imp_tol", C.c_double), ("lanes", C.c_int), ("pvm_k", C.c_int),
-                ("pvm_products", C.c_int)]
+                ("pvm_products", C.c_int), ("solver", C.c_int)]
 
 
 class rrmhd_tuning(C.Structure):
@@ -177,6 +177,8 @@ def make_opts(**kw):
             k, v = "beta_mode", int(bool(v))
         if k == "pvm_products" and isinstance(v, str):
             v = {"fd": 0, "tangent": 1}[v]
+        if k == "solver" and isinstance(v, str):
+            v = {"pvm": 0, "radhll": 1}[v]
         setattr(o, k, v)
     return o
 
