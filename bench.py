@@ -288,6 +288,41 @@ def measure(a, precision, rank, world, local):
     return out
 
 
+def measure_variant(a, opts, tuning, steps=5):
+    """Zone-updates/s of the C1 batch (FP64) with other solver options: the paper's
+    variants timed beside PVM-int-8.  Same seed and launch shapes as the FP64 line;
+    warm-up 2 steps, then `steps` steps timed with CUDA events."""
+    import torch
+
+    from paper_2212_00370_gb300 import rrmhd
+    from paper_2212_00370_gb300 import workloads as W
+
+    w = W.riemann_batch(a.instances, seed=W.SEED_BASE + 1)
+    grids = [rrmhd.make_grid(1, g["n"], g["dx"], g["bc"]) for g in w.grids]
+    ctx = rrmhd.Context(grids, gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl, precision="fp64", **opts)
+    if tuning:
+        ctx.set_tuning(**tuning)
+    ctx.set_opacity(torch.tensor(w.kappa, device="cuda"), torch.tensor(w.sigma, device="cuda"))
+    ctx.set_state(torch.tensor(w.V, device="cuda"))
+    ctx.set_times(np.zeros(w.n_inst), np.full(w.n_inst, np.inf))
+    n_cells = np.array([g["n"][0] for g in w.grids], dtype=np.int64)
+    stream = torch.cuda.current_stream()
+    ctx.imex_step(2)
+    torch.cuda.synchronize()
+    st0 = ctx.inst_status()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.imex_step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    live = (st0 == 0) & (ctx.inst_status() == 0)
+    launches = ctx.launches_per_step() * steps
+    ctx.close()
+    return {"value": float(n_cells[live].sum()) * 1e3 / ms, "ms_per_step": ms, "steps": steps,
+            "failed_instances": int((~live).sum()), "launches": launches}
+
+
 def measure_serving(a, tuning=None):
     """C4 serving sample: the first `serve_requests` requests of the C4 arrival process
     (Poisson, 200 requests/s; 70 % 1D N~U{256..4096}, 30 % planar 2D side~U{128..512};
@@ -398,6 +433,15 @@ def run_ours(a, rank, world, pool, cores):
                                "note": "FP64 with exact tangent Jacobian products instead of the "
                                        "paper's eps = 1e-8 flux differences (a variant)"}
         out["gpu_launches"] += g["gpu_launches"]
+        # the paper's variants, FP64, same workload and shapes as the FP64 line
+        variants = {}
+        for name, opts in (("radhll", {"solver": "radhll"}), ("pvm_int16", {"pvm_k": 4})):
+            variants[name] = measure_variant(a, opts, f["tuning"])
+            out["gpu_launches"] += variants[name].pop("launches")
+        variants["pvm_int8_time_over_radhll"] = variants["radhll"]["value"] / f["value"]
+        variants["note"] = ("FP64 zone-updates/s of Rad-HLL (Sec. 3.2.1) and PVM-int-16 on the "
+                            "C1 batch; the paper reports PVM-int-8 costing ~2x HLL in CPU time")
+        out["fp64_variants"] = variants
     if a.serve_requests > 0 and world == 1:
         out["serving"] = measure_serving(a, res["fp32_bulk"]["tuning"] if "fp32_bulk" in res else None)
     if rank == 0 and pool is not None:

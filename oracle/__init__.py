@@ -135,6 +135,14 @@ def lib():
             "or_grid_step_c": (C.c_int, [P, G, C.c_double, dp, dp, dp, dp, dp, S]),
             "or_grid_run": (C.c_int, [P, G, C.c_double, C.c_double, C.c_int, dp, dp, dp, dp,
                                       dp, C.POINTER(C.c_int), S]),
+            "or_grid_step_ct": (C.c_int, [P, G, C.c_double, dp, dp, dp, dp, dp, dp, S]),
+            "or_grid_run_ct": (C.c_int, [P, G, C.c_double, C.c_double, C.c_int, dp, dp, dp, dp, dp,
+                                         dp, C.POINTER(C.c_int), S]),
+            "or_grid_face_flux_b": (C.c_int, [P, G, C.c_int, dp, dp, dp, dp, dp, dp, S]),
+            "or_ct_nfaces": (C.c_int64, [G]),
+            "or_ct_faces_from_cells": (None, [G, dp, dp]),
+            "or_ct_cells_from_faces": (None, [G, dp, dp, dp]),
+            "or_ct_div": (None, [G, dp, dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -369,31 +377,64 @@ def stage(g, s, dt, U0, Us, Vs, kappa, sigma, P, stats=None):
     return Uo, Vo, cs, nf
 
 
-def step(g, dt, U, V, kappa, sigma, P, stats=None, jcache=None):
+def step(g, dt, U, V, kappa, sigma, P, stats=None, jcache=None, bface=None):
     """One IMEX-RK3 step in place; returns the number of failed cells.  jcache: a
-    float64 array of 17 * ncells (zeros = empty) carried between steps, or None."""
+    float64 array of 17 * ncells (zeros = empty) carried between steps, or None.
+    bface: the staggered field of constrained transport (2D/3D; ct_nfaces(g)
+    values, advanced in place), or None."""
     N = g.ncells
     assert U.flags.c_contiguous and V.flags.c_contiguous and U.dtype == np.float64
     k = np.ascontiguousarray(kappa, dtype=np.float64).reshape(-1)
     s = np.ascontiguousarray(sigma, dtype=np.float64).reshape(-1)
     assert U.size == 12 * N
-    if jcache is None:
+    if jcache is None and bface is None:
         return lib().or_grid_step(C.byref(P.struct()), C.byref(g.struct()), float(dt), _d(U),
                                   _d(V), _d(k), _d(s), _stats(stats))
+    if jcache is None:
+        jcache = np.zeros(17 * N)
     assert jcache.size == 17 * N and jcache.dtype == np.float64 and jcache.flags.c_contiguous
-    return lib().or_grid_step_c(C.byref(P.struct()), C.byref(g.struct()), float(dt), _d(U),
-                                _d(V), _d(k), _d(s), _d(jcache), _stats(stats))
+    if bface is None:
+        return lib().or_grid_step_c(C.byref(P.struct()), C.byref(g.struct()), float(dt), _d(U),
+                                    _d(V), _d(k), _d(s), _d(jcache), _stats(stats))
+    assert bface.flags.c_contiguous and bface.dtype == np.float64 and bface.size == ct_nfaces(g)
+    return lib().or_grid_step_ct(C.byref(P.struct()), C.byref(g.struct()), float(dt), _d(U), _d(V),
+                                 _d(bface), _d(k), _d(s), _d(jcache), _stats(stats))
 
 
-def run(g, t0, t_end, U, V, kappa, sigma, P, max_steps=10 ** 9, stats=None):
-    """Advance in place to t_end (last step clipped); returns (t, steps, nfail)."""
+def run(g, t0, t_end, U, V, kappa, sigma, P, max_steps=10 ** 9, stats=None, bface=None):
+    """Advance in place to t_end (last step clipped); returns (t, steps, nfail).
+    bface: staggered field of constrained transport (advanced in place), or None."""
     N = g.ncells
     assert U.flags.c_contiguous and V.flags.c_contiguous and U.size == 12 * N
     k = np.ascontiguousarray(kappa, dtype=np.float64).reshape(-1)
     s = np.ascontiguousarray(sigma, dtype=np.float64).reshape(-1)
     t = C.c_double(0.0)
     ns = C.c_int(0)
-    nf = lib().or_grid_run(C.byref(P.struct()), C.byref(g.struct()), float(t0), float(t_end),
-                           int(max_steps), _d(U), _d(V), _d(k), _d(s), C.byref(t), C.byref(ns),
-                           _stats(stats))
+    if bface is not None:
+        assert bface.flags.c_contiguous and bface.dtype == np.float64 and bface.size == ct_nfaces(g)
+    nf = lib().or_grid_run_ct(C.byref(P.struct()), C.byref(g.struct()), float(t0), float(t_end),
+                              int(max_steps), _d(U), _d(V), None if bface is None else _d(bface),
+                              _d(k), _d(s), C.byref(t), C.byref(ns), _stats(stats))
     return t.value, ns.value, nf
+
+
+def ct_nfaces(g):
+    """Faces of the staggered field (directions d < ndim, one after the other)."""
+    return int(lib().or_ct_nfaces(C.byref(g.struct())))
+
+
+def ct_faces_from_cells(g, V):
+    b = np.empty(ct_nfaces(g))
+    lib().or_ct_faces_from_cells(C.byref(g.struct()), _d(np.ascontiguousarray(V)), _d(b))
+    return b
+
+
+def ct_cells_from_faces(g, bface, U, V):
+    """Sets the cell-centred B_d (d < ndim) of U and V (in place) to the face means."""
+    lib().or_ct_cells_from_faces(C.byref(g.struct()), _d(bface), _d(U), _d(V))
+
+
+def ct_div(g, bface):
+    div = np.empty(g.ncells)
+    lib().or_ct_div(C.byref(g.struct()), _d(bface), _d(div))
+    return div

@@ -10,7 +10,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["physics.c", "scheme.c", "implicit.c", "grid.c"]
+SOURCES = ["physics.c", "scheme.c", "implicit.c", "grid.c", "ct.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 CFLAGS = ["-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
           "-Wall", "-Wno-unused-function"]

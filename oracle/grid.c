@@ -69,6 +69,16 @@ int or_grid_face_flux(const or_params* P, const or_grid* g, int dir, const doubl
                       const double* V, const double* kappa, const double* sigma,
                       double* Fhat, or_stats* st)
 {
+    return or_grid_face_flux_b(P, g, dir, U, V, kappa, sigma, 0, Fhat, st);
+}
+
+/* Same, with the normal field component of both face states taken from the
+ * staggered field bdir (the faces of direction dir; constrained transport) when
+ * bdir is not NULL. */
+int or_grid_face_flux_b(const or_params* P, const or_grid* g, int dir, const double* U,
+                        const double* V, const double* kappa, const double* sigma,
+                        const double* bdir, double* Fhat, or_stats* st)
+{
     int64_t N = ncells(g);
     int m[3];
     face_dims(g, dir, m);
@@ -92,6 +102,11 @@ int or_grid_face_flux(const or_params* P, const or_grid* g, int dir, const doubl
                 or_reconstruct(P, w[1], w[2], w[3], VR, Vp, 0); /* cell f:   left face  */
                 double tauL = (U[cidx[1]] * (kappa[cidx[1]] + sigma[cidx[1]])) * g->dx[dir];
                 double tauR = (U[cidx[2]] * (kappa[cidx[2]] + sigma[cidx[2]])) * g->dx[dir];
+                if (bdir) {
+                    double bn = bdir[((int64_t)k * m[1] + j) * m[0] + i];
+                    VL[5 + dir] = bn;
+                    VR[5 + dir] = bn;
+                }
                 if (P->solver == OR_SOLVER_RADHLL)
                     or_radhll_flux(P, dir, VL, VR, tauL, tauR, F);
                 else
@@ -111,6 +126,7 @@ typedef struct {
     int m[3][3];
     const double *U0, *Us, *Vs, *kappa, *sigma;
     double* jc;   /* per-cell Jacobian cache, [17][N] planes, or NULL */
+    const double* bface;   /* the stage's new staggered field (constrained transport), or NULL */
 } stage_ctx;
 
 /* U* of one cell from its face fluxes, then the implicit solve (Sec. 3.3). */
@@ -138,6 +154,11 @@ static int cell_update(const stage_ctx* s, int i, int j, int k, double Un[12], d
         else
             Ust[q] = s->a * s->U0[q * N + c] + s->b * (s->Us[q * N + c] - acc);
     }
+    if (s->bface)   /* constrained transport: B_d is the mean of the two staggered faces */
+        for (int d = 0; d < g->ndim; d++) {
+            int64_t base = or_ct_face_base(g, d);
+            Ust[5 + d] = 0.5 * (s->bface[base + fl[d]] + s->bface[base + fr[d]]);
+        }
     load(s->Vs, N, c, vs);
     double Zg = or_prim_Z(s->P, vs);
     if (!s->jc) return or_implicit(s->P, s->kappa[c], s->sigma[c], s->hdt, Ust, Zg, Un, Vn, st);
@@ -166,9 +187,25 @@ int or_grid_stage_c(const or_params* P, const or_grid* g, int stage, double dt,
                     const double* kappa, const double* sigma,
                     double* Uout, double* Vout, int32_t* cell_status, double* jcache, or_stats* st)
 {
+    return or_grid_stage_ct(P, g, stage, dt, U0, Us, Vs, kappa, sigma, 0, 0, 0, Uout, Vout,
+                            cell_status, jcache, st);
+}
+
+/* One stage with constrained transport when b0 is not NULL (2D/3D): the face
+ * fluxes take the normal field from bs, the staggered field advances to bout
+ * (ct.c), the cell-centred B of U* is the mean of bout's faces, and the
+ * admissibility fallback replaces all but the magnetic fluxes. */
+int or_grid_stage_ct(const or_params* P, const or_grid* g, int stage, double dt,
+                     const double* U0, const double* Us, const double* Vs,
+                     const double* kappa, const double* sigma,
+                     const double* b0, const double* bs, double* bout,
+                     double* Uout, double* Vout, int32_t* cell_status, double* jcache, or_stats* st)
+{
     int64_t N = ncells(g);
+    const int ct = b0 && g->ndim >= 2;
     stage_ctx s;
     s.jc = jcache;
+    s.bface = ct ? bout : 0;
     s.P = P;
     s.g = g;
     s.stage = stage;
@@ -182,8 +219,10 @@ int or_grid_stage_c(const or_params* P, const or_grid* g, int stage, double dt,
     for (int d = 0; d < g->ndim; d++) {
         face_dims(g, d, s.m[d]);
         s.Fh[d] = (double*)malloc(sizeof(double) * 12 * (size_t)s.m[d][0] * s.m[d][1] * s.m[d][2]);
-        or_grid_face_flux(P, g, d, Us, Vs, kappa, sigma, s.Fh[d], st);
+        or_grid_face_flux_b(P, g, d, Us, Vs, kappa, sigma, ct ? bs + or_ct_face_base(g, d) : 0,
+                            s.Fh[d], st);
     }
+    if (ct) or_ct_stage(g, stage, dt, s.Fh, Vs, b0, bs, bout);
     s.a = 0.0;
     s.b = 1.0;
     double w = 1.0;
@@ -230,7 +269,8 @@ int or_grid_stage_c(const or_params* P, const or_grid* g, int stage, double dt,
                         load(Vs, N, cr, vr);
                         or_llf_flux(P, d, vl, vr, F);
                         int64_t fi = ((int64_t)k * s.m[d][1] + j) * s.m[d][0] + i;
-                        for (int q = 0; q < 12; q++) s.Fh[d][q * NF + fi] = F[q];
+                        for (int q = 0; q < 12; q++)
+                            if (!ct || q < 5 || q > 7) s.Fh[d][q * NF + fi] = F[q];
                     }
         }
         /* update again every cell with a changed face: flagged or next to one */
@@ -280,24 +320,44 @@ int or_grid_stage(const or_params* P, const or_grid* g, int stage, double dt,
 int or_grid_step_c(const or_params* P, const or_grid* g, double dt, double* U, double* V,
                    const double* kappa, const double* sigma, double* jcache, or_stats* st)
 {
+    return or_grid_step_ct(P, g, dt, U, V, 0, kappa, sigma, jcache, st);
+}
+
+/* One step; bface (constrained transport, 2D/3D, may be NULL) is advanced in
+ * place with U and V. */
+int or_grid_step_ct(const or_params* P, const or_grid* g, double dt, double* U, double* V,
+                    double* bface, const double* kappa, const double* sigma, double* jcache,
+                    or_stats* st)
+{
     int64_t N = ncells(g);
     size_t bytes = sizeof(double) * 12 * (size_t)N;
     double* U1 = (double*)malloc(bytes);
     double* V1 = (double*)malloc(bytes);
     double* U2 = (double*)malloc(bytes);
     double* V2 = (double*)malloc(bytes);
+    const int ct = bface && g->ndim >= 2;
+    size_t fb = ct ? sizeof(double) * (size_t)or_ct_nfaces(g) : 0;
+    double* b1 = ct ? (double*)malloc(fb) : 0;
+    double* b2 = ct ? (double*)malloc(fb) : 0;
+    const double* b0 = ct ? bface : 0;
+    if (ct) or_ct_canonical(g, bface);
     int nfail = 0;
-    nfail += or_grid_stage_c(P, g, 1, dt, U, U, V, kappa, sigma, U1, V1, 0, jcache, st);
-    if (!nfail) nfail += or_grid_stage_c(P, g, 2, dt, U, U1, V1, kappa, sigma, U2, V2, 0, jcache, st);
-    if (!nfail) nfail += or_grid_stage_c(P, g, 3, dt, U, U2, V2, kappa, sigma, U1, V1, 0, jcache, st);
+    nfail += or_grid_stage_ct(P, g, 1, dt, U, U, V, kappa, sigma, b0, b0, b1, U1, V1, 0, jcache, st);
+    if (!nfail)
+        nfail += or_grid_stage_ct(P, g, 2, dt, U, U1, V1, kappa, sigma, b0, b1, b2, U2, V2, 0, jcache, st);
+    if (!nfail)
+        nfail += or_grid_stage_ct(P, g, 3, dt, U, U2, V2, kappa, sigma, b0, b2, b1, U1, V1, 0, jcache, st);
     if (!nfail) {
         memcpy(U, U1, bytes);
         memcpy(V, V1, bytes);
+        if (ct) memcpy(bface, b1, fb);
     }
     free(U1);
     free(V1);
     free(U2);
     free(V2);
+    free(b1);
+    free(b2);
     return nfail;
 }
 
@@ -314,6 +374,13 @@ int or_grid_run(const or_params* P, const or_grid* g, double t0, double t_end, i
                 double* U, double* V, const double* kappa, const double* sigma,
                 double* t_out, int* steps_out, or_stats* st)
 {
+    return or_grid_run_ct(P, g, t0, t_end, max_steps, U, V, 0, kappa, sigma, t_out, steps_out, st);
+}
+
+int or_grid_run_ct(const or_params* P, const or_grid* g, double t0, double t_end, int max_steps,
+                   double* U, double* V, double* bface, const double* kappa, const double* sigma,
+                   double* t_out, int* steps_out, or_stats* st)
+{
     double t = t0;
     int s = 0, nfail = 0;
     double* jc = (double*)calloc((size_t)17 * ncells(g), sizeof(double));
@@ -324,7 +391,7 @@ int or_grid_run(const or_params* P, const or_grid* g, double t0, double t_end, i
             nfail = 1;
             break;
         }
-        nfail = or_grid_step_c(P, g, dt, U, V, kappa, sigma, jc, st);
+        nfail = or_grid_step_ct(P, g, dt, U, V, bface, kappa, sigma, jc, st);
         if (nfail) break;
         t = t + dt;
         s++;

@@ -136,6 +136,31 @@ int    or_grid_run(const or_params* P, const or_grid* g, double t0, double t_end
                    double* U, double* V, const double* kappa, const double* sigma,
                    double* t_out, int* steps_out, or_stats* st);
 
+/* ---- constrained transport (ct.c; grid.c *_ct, *_b variants) ---- */
+int    or_grid_face_flux_b(const or_params* P, const or_grid* g, int dir, const double* U,
+                           const double* V, const double* kappa, const double* sigma,
+                           const double* bdir, double* Fhat, or_stats* st);
+int    or_grid_stage_ct(const or_params* P, const or_grid* g, int stage, double dt,
+                        const double* U0, const double* Us, const double* Vs,
+                        const double* kappa, const double* sigma,
+                        const double* b0, const double* bs, double* bout,
+                        double* Uout, double* Vout, int32_t* cell_status, double* jcache,
+                        or_stats* st);
+int    or_grid_step_ct(const or_params* P, const or_grid* g, double dt, double* U, double* V,
+                       double* bface, const double* kappa, const double* sigma, double* jcache,
+                       or_stats* st);
+int    or_grid_run_ct(const or_params* P, const or_grid* g, double t0, double t_end, int max_steps,
+                      double* U, double* V, double* bface, const double* kappa, const double* sigma,
+                      double* t_out, int* steps_out, or_stats* st);
+int64_t or_ct_face_base(const or_grid* g, int d);
+int64_t or_ct_nfaces(const or_grid* g);
+void   or_ct_faces_from_cells(const or_grid* g, const double* V, double* bface);
+void   or_ct_cells_from_faces(const or_grid* g, const double* bface, double* U, double* V);
+void   or_ct_div(const or_grid* g, const double* bface, double* div);
+void   or_ct_canonical(const or_grid* g, double* bface);
+void   or_ct_stage(const or_grid* g, int stage, double dt, double* const Fh[3], const double* V,
+                   const double* b0, const double* bs, double* bout);
+
 /* ---- vectorised helpers for the Python wrapper (physics.c) ---- */
 void or_prim2con_n(const or_params* P, int64_t n, const double* V, double* U);
 void or_con2prim_n(const or_params* P, int64_t n, const double* U, const double* Zg,
