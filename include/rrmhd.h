@@ -94,6 +94,12 @@ typedef struct {
                           magnetosonic speeds for the magnetofluid and lambda_r1/lambda_r3
                           (Eqs. lam1-lam3) for the radiation, the latter capped at
                           4/(3 tau) (Eq. limits) when beta_mode = 1                      */
+    int    ct;         /* 1: constrained transport of the magnetic field on 2D/3D instances
+                          (CT-contact EMFs of Gardiner & Stone 2005, the scheme the paper's
+                          multi-D runs use, Sec. 4): the normal field lives on the faces,
+                          cell-centred B is the mean of the two faces, and the discrete
+                          divergence is kept to round-off.  FP64 only.  0: cell-centred B
+                          updated by its fluxes (default).                               */
 } rrmhd_opts;
 
 typedef struct rrmhd_ctx rrmhd_ctx;
@@ -236,6 +242,18 @@ rrmhd_status rrmhd_set_tuning(rrmhd_ctx* ctx, const rrmhd_tuning* t);
  * NULL) receives them, best_ms (host, may be NULL) the median step time.  Allocates
  * a copy of the state for the duration of the call (ENOMEM if that fails). */
 rrmhd_status rrmhd_autotune(rrmhd_ctx* ctx, int repeats, rrmhd_tuning* best, double* best_ms);
+
+/* Staggered magnetic field of a context with opts.ct = 1: one value per face, the
+ * component normal to the face, in the face layout of the fluxes (directions 0, 1, 2
+ * one after the other, num_faces(dir) each; 1D instances' faces are unused).
+ * rrmhd_set_state starts it from the cell-centred B (mean of the two cells next to
+ * each face).  rrmhd_set_face_field replaces it (a divergence-free field should come
+ * from a discrete vector potential); in periodic directions the faces at index 0 and
+ * n are the same face, and face 0's value is kept for both.  Either call then resets
+ * the cell-centred B of the state to the face means and recomputes U.  b: device
+ * double[sum_dir num_faces(dir)].  EINVAL if opts.ct is 0. */
+rrmhd_status rrmhd_set_face_field(rrmhd_ctx* ctx, const double* b);
+rrmhd_status rrmhd_get_face_field(const rrmhd_ctx* ctx, double* b);
 
 /* rho h W^2 of primitives: V double[12][n] -> Z double[n] (con2prim warm starts). */
 rrmhd_status rrmhd_prim_z(rrmhd_ctx* ctx, const double* V, double* Z, int64_t n);

@@ -143,6 +143,7 @@ def lib():
             "or_ct_faces_from_cells": (None, [G, dp, dp]),
             "or_ct_cells_from_faces": (None, [G, dp, dp, dp]),
             "or_ct_div": (None, [G, dp, dp]),
+            "or_ct_canonical": (None, [G, dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -432,6 +433,11 @@ def ct_faces_from_cells(g, V):
 def ct_cells_from_faces(g, bface, U, V):
     """Sets the cell-centred B_d (d < ndim) of U and V (in place) to the face means."""
     lib().or_ct_cells_from_faces(C.byref(g.struct()), _d(bface), _d(U), _d(V))
+
+
+def ct_canonical(g, bface):
+    """Periodic duplicate faces (index n_d) take the value of face 0 (in place)."""
+    lib().or_ct_canonical(C.byref(g.struct()), _d(bface))
 
 
 def ct_div(g, bface):

@@ -7,6 +7,10 @@
 //   faces  : direction-major; faces normal to d of instance i are
 //            [dir_base[d] + face_off[d][i], ... + nfaces(i,d)), each instance's
 //            block row-major over (n + e_d) with x fastest;  Fhat is [12][nfaces].
+//   edges  : (constrained transport, 2D/3D instances) direction-major like the
+//            faces; edges along e of instance i are [edge_base[e] + edge_off[e][i],
+//            ...), row-major over m_d = n_d + 1 for the directions d != e in use
+//            (2D: edges along z only).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -22,6 +26,7 @@ struct InstDesc {
   double dx[3];
   int64_t cell_off;
   int64_t face_off[3];  // within the direction's block
+  int64_t edge_off[3];  // within the edge direction's block (constrained transport)
 };
 
 // Per-instance time-stepping state (device arrays of length n_inst).
@@ -41,12 +46,16 @@ struct Batch {
   const InstDesc* inst;      // [n_inst]
   const int64_t* cell_off;   // [n_inst + 1]
   const int64_t* face_off;   // [3][n_inst + 1] (prefix sums within each direction)
+  const int64_t* edge_off;   // [3][n_inst + 1] (constrained transport)
+  int64_t edge_base[4];      // edges along e: [edge_base[e], edge_base[e+1])
   InstState st;
   // the part of the batch a launch covers (a lane: contiguous instances)
   int i_begin, i_end;        // instances
   int64_t c_begin, c_end;    // cells
   int64_t f_begin[3];        // faces of direction d: [f_begin[d], f_begin[d] + f_count[d])
   int64_t f_count[3];
+  int64_t e_begin[3];        // edges along e: [e_begin[e], e_begin[e] + e_count[e])
+  int64_t e_count[3];
 };
 
 struct StageArgs {
@@ -70,6 +79,14 @@ struct StageArgs {
   uint8_t* bad;            // [ncells] cells whose U* is inadmissible (admissibility fallback)
   double* jc;              // [17][ncells] per-cell Jacobian cache of the implicit solve
   unsigned long long* work;  // [2] chunk counters of persistent face / cell launches
+  // constrained transport (2D/3D instances when ct != 0): the staggered normal
+  // field per face (one value per face, the face layout) at the step start (b0),
+  // the stage input (bs) and output (bout); the edge EMFs of the stage.
+  int ct;
+  const double* b0;
+  const double* bs;
+  double* bout;
+  double* emf;
 };
 
 // How a kernel spreads its work items over threads (launch_shape.cuh).
@@ -89,6 +106,13 @@ void launch_faces_f64(const StageArgs& a, const LaunchShape& sh, cudaStream_t s)
 void launch_cells_f64(const StageArgs& a, const LaunchShape& sh, cudaStream_t s);
 void launch_fallback_f64(const StageArgs& a, cudaStream_t s);
 void launch_signal_f64(const Params& P, const Batch& b, const double* V, cudaStream_t s);
+// constrained transport: edge EMFs (CT-contact) and the face-field stage update
+void launch_emf_f64(const StageArgs& a, cudaStream_t s);
+void launch_bface_f64(const StageArgs& a, cudaStream_t s);
+// face field <-> cell-centred B (set-up), and periodic duplicate faces made equal
+void launch_faces_from_cells_f64(const Batch& b, const double* V, double* bface, cudaStream_t s);
+void launch_cells_from_faces_f64(const Batch& b, const double* bface, double* V, cudaStream_t s);
+void launch_ct_canonical_f64(const Batch& b, double* bface, cudaStream_t s);
 
 // FP32-bulk form: FP32 faces (tangent PVM products), FP64 cells
 void launch_faces_f32(const StageArgs& a, const LaunchShape& sh, cudaStream_t s);

@@ -70,6 +70,74 @@ static __device__ __forceinline__ FacePos face_pos(const Batch& b, int64_t g) {
   return q;
 }
 
+// Edge t of the launch's edge ranges (constrained transport): direction e,
+// instance, position (edge dims m_d = n_d + 1 for d != e, d < ndim).
+struct EdgePos {
+  int e, i, pos[3];
+  int64_t g;  // global edge index
+  InstDesc I;
+};
+
+static __device__ __forceinline__ int64_t lane_edges(const Batch& b) {
+  return b.e_count[0] + b.e_count[1] + b.e_count[2];
+}
+
+static __device__ __forceinline__ EdgePos edge_pos(const Batch& b, int64_t t) {
+  EdgePos q;
+  q.e = 0;
+  while (q.e < 2 && t >= b.e_count[q.e]) {
+    t -= b.e_count[q.e];
+    ++q.e;
+  }
+  q.g = b.e_begin[q.e] + t;
+  const int64_t g = q.g - b.edge_base[q.e];
+  const int64_t* off = b.edge_off + (int64_t)q.e * (b.n_inst + 1);
+  q.i = find_inst(off, b.i_begin, b.i_end, g);
+  q.I = b.inst[q.i];
+  const int64_t le = g - off[q.i];
+  int m[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) m[d] = q.I.n[d] + ((d != q.e && d < q.I.ndim) ? 1 : 0);
+  q.pos[0] = (int)(le % m[0]);
+  const int64_t r = le / m[0];
+  q.pos[1] = (int)(r % m[1]);
+  q.pos[2] = (int)(r / m[1]);
+  return q;
+}
+
+// Global index of the face of direction d at p (p[d] the face index along d, the
+// other entries cell indices mapped through the boundaries).
+static __device__ __forceinline__ int64_t face_gidx(const Batch& b, const InstDesc& I, int d,
+                                                   const int p[3]) {
+  int q[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) q[e] = (e == d) ? p[e] : map_idx(p[e], I.n[e], I.bc[e]);
+  const int m0 = I.n[0] + (d == 0), m1 = I.n[1] + (d == 1);
+  return b.dir_base[d] + I.face_off[d] + ((int64_t)q[2] * m1 + q[1]) * m0 + q[0];
+}
+
+// Global index of the cell at p (mapped through the boundaries).
+static __device__ __forceinline__ int64_t cell_gidx(const InstDesc& I, const int p[3]) {
+  int q[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) q[e] = map_idx(p[e], I.n[e], I.bc[e]);
+  return I.cell_off + ((int64_t)q[2] * I.n[1] + q[1]) * I.n[0] + q[0];
+}
+
+// Whether instance I has edges along e (constrained transport).
+static __device__ __forceinline__ bool has_edges(const InstDesc& I, int e) {
+  return I.ndim == 3 || (I.ndim == 2 && e == 2);
+}
+
+// Global index of the edge along e at q (edge dims n_d + 1 for d != e, d < ndim).
+static __device__ __forceinline__ int64_t edge_gidx(const Batch& b, const InstDesc& I, int e,
+                                                   const int q[3]) {
+  int m[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) m[d] = I.n[d] + ((d != e && d < I.ndim) ? 1 : 0);
+  return b.edge_base[e] + I.edge_off[e] + ((int64_t)q[2] * m[1] + q[1]) * m[0] + q[0];
+}
+
 struct CellPos {
   int i;       // instance
   int p[3];    // position in the instance's grid

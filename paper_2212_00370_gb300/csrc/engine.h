@@ -41,7 +41,8 @@ inline bool opts_ok(const rrmhd_opts& o) {
          o.recon <= 3 && o.c2p_maxit >= 1 && o.imp_maxit >= 1 && o.imp_tol > 0.0 &&
          (o.precision == RRMHD_FP64 || o.precision == RRMHD_FP32_BULK) && o.lanes >= 1 &&
          (o.pvm_k == 3 || o.pvm_k == 4) && (o.pvm_products == 0 || o.pvm_products == 1) &&
-         (o.solver == RRMHD_SOLVER_PVM || o.solver == RRMHD_SOLVER_RADHLL);
+         (o.solver == RRMHD_SOLVER_PVM || o.solver == RRMHD_SOLVER_RADHLL) &&
+         (o.ct == 0 || (o.ct == 1 && o.precision == RRMHD_FP64));
 }
 
 inline bool grid_ok(const rrmhd_grid& g, std::string& why) {
@@ -88,6 +89,15 @@ inline int64_t grid_faces(const rrmhd_grid& g) {
   return grid_faces(g, 0) + grid_faces(g, 1) + grid_faces(g, 2);
 }
 
+// Edges along e of a grid for constrained transport: 2D grids have edges along z
+// only, 3D grids along all three; 1D grids none.
+inline int64_t grid_edges(const rrmhd_grid& g, int e) {
+  if (g.ndim < 2 || (g.ndim == 2 && e != 2)) return 0;
+  int64_t c = 1;
+  for (int d = 0; d < 3; ++d) c *= g.n[d] + ((d != e && d < g.ndim) ? 1 : 0);
+  return c;
+}
+
 // Packed layout of a list of instances: cells back to back, faces direction-major
 // with per-instance blocks (batch.h).
 struct Layout {
@@ -95,8 +105,10 @@ struct Layout {
   std::vector<InstDesc> inst;
   std::vector<int64_t> cell_off;  // [n_inst + 1]
   std::vector<int64_t> face_off;  // [3][n_inst + 1], prefix sums within each direction
-  int64_t ncells = 0, nfaces = 0;
+  std::vector<int64_t> edge_off;  // [3][n_inst + 1], prefix sums within each edge direction
+  int64_t ncells = 0, nfaces = 0, nedges = 0;
   int64_t dir_base[4] = {0, 0, 0, 0};
+  int64_t edge_base[4] = {0, 0, 0, 0};
 };
 
 inline Layout make_layout(const rrmhd_grid* grids, int n_inst) {
@@ -105,6 +117,7 @@ inline Layout make_layout(const rrmhd_grid* grids, int n_inst) {
   L.inst.resize(n_inst);
   L.cell_off.assign(n_inst + 1, 0);
   L.face_off.assign(3 * (size_t)(n_inst + 1), 0);
+  L.edge_off.assign(3 * (size_t)(n_inst + 1), 0);
   for (int i = 0; i < n_inst; ++i) {
     const rrmhd_grid& g = grids[i];
     InstDesc& I = L.inst[i];
@@ -120,12 +133,18 @@ inline Layout make_layout(const rrmhd_grid* grids, int n_inst) {
       int64_t* fo = &L.face_off[(size_t)d * (n_inst + 1)];
       I.face_off[d] = fo[i];
       fo[i + 1] = fo[i] + grid_faces(g, d);
+      int64_t* eo = &L.edge_off[(size_t)d * (n_inst + 1)];
+      I.edge_off[d] = eo[i];
+      eo[i + 1] = eo[i] + grid_edges(g, d);
     }
   }
   L.ncells = L.cell_off[n_inst];
   for (int d = 0; d < 3; ++d)
     L.dir_base[d + 1] = L.dir_base[d] + L.face_off[(size_t)d * (n_inst + 1) + n_inst];
   L.nfaces = L.dir_base[3];
+  for (int d = 0; d < 3; ++d)
+    L.edge_base[d + 1] = L.edge_base[d] + L.edge_off[(size_t)d * (n_inst + 1) + n_inst];
+  L.nedges = L.edge_base[3];
   return L;
 }
 
@@ -159,10 +178,13 @@ struct DeviceBufs {
   double* Fhat = nullptr;  // [12][nfaces] FP64, or [12][nfaces] FP32 in the FP32-bulk form
   uint8_t* bad = nullptr;  // admissibility-fallback flags, one per cell
   double* jc = nullptr;    // per-cell Jacobian cache of the implicit solve, [17][ncells]
+  // constrained transport: staggered face field sets (with U0/V0, Ua/Va, Ub/Vb), EMFs
+  double *bf0 = nullptr, *bfa = nullptr, *bfb = nullptr, *emf = nullptr;
   // per instance
   InstDesc* inst = nullptr;
   int64_t* cell_off = nullptr;
   int64_t* face_off = nullptr;  // [3][n_inst + 1]
+  int64_t* edge_off = nullptr;  // [3][n_inst + 1]
   double *t = nullptr, *t_end = nullptr, *dt = nullptr;
   unsigned long long* smax = nullptr;
   int* status = nullptr;
@@ -178,6 +200,8 @@ inline Batch make_batch(const Layout& L, const DeviceBufs& B, int i0, int i1) {
   b.inst = B.inst;
   b.cell_off = B.cell_off;
   b.face_off = B.face_off;
+  b.edge_off = B.edge_off;
+  for (int d = 0; d < 4; ++d) b.edge_base[d] = L.edge_base[d];
   b.st.t = B.t;
   b.st.t_end = B.t_end;
   b.st.dt = B.dt;
@@ -191,6 +215,9 @@ inline Batch make_batch(const Layout& L, const DeviceBufs& B, int i0, int i1) {
     const int64_t* fo = &L.face_off[(size_t)d * (L.n_inst + 1)];
     b.f_begin[d] = L.dir_base[d] + fo[i0];
     b.f_count[d] = fo[i1] - fo[i0];
+    const int64_t* eo = &L.edge_off[(size_t)d * (L.n_inst + 1)];
+    b.e_begin[d] = L.edge_base[d] + eo[i0];
+    b.e_count[d] = eo[i1] - eo[i0];
   }
   return b;
 }
@@ -220,6 +247,10 @@ inline StageArgs stage_args(const Params& P, const DeviceBufs& B, const Batch& b
   a.bad = B.bad;
   a.jc = B.jc;
   a.work = work;
+  a.ct = 0;
+  a.b0 = a.bs = nullptr;
+  a.bout = nullptr;
+  a.emf = B.emf;
   return a;
 }
 
@@ -244,9 +275,14 @@ inline void launch_fallback(int precision, const StageArgs& a, cudaStream_t s) {
     launch_fallback_f64(a, s);
 }
 
-// The three launch groups of one stage in the given precision and shapes.
+// The launch groups of one stage in the given precision and shapes: faces, then
+// (constrained transport) edge EMFs and the face-field update, cells, fallback.
 inline void launch_stage(int precision, const Tuning& tu, const StageArgs& a, cudaStream_t s) {
   launch_faces(precision, a, tu.faces, s);
+  if (a.ct) {
+    launch_emf_f64(a, s);
+    launch_bface_f64(a, s);
+  }
   launch_cells(precision, a, tu.cells, s);
   launch_fallback(precision, a, s);
 }
@@ -264,16 +300,30 @@ inline bool tuning_ok(const Tuning& t) {
 // inputs, so the admissibility fallback can re-read them.  Launches: begin,
 // 3 x {faces, cells, fallback faces, fallback cells}, end.
 // work: this stream's two chunk counters (persistent shapes).
+// ct: constrained transport on (the face-field sets rotate with the state).
 inline void enqueue_step(const Params& P, int precision, const Tuning& tu, const DeviceBufs& B,
-                         const Batch& b, int cur, unsigned long long* work, cudaStream_t s) {
+                         const Batch& b, int cur, unsigned long long* work, cudaStream_t s,
+                         int ct = 0) {
   double* AU = cur ? B.Ua : B.U0;
   double* AV = cur ? B.Va : B.V0;
   double* BU = cur ? B.U0 : B.Ua;
   double* BV = cur ? B.V0 : B.Va;
+  double* Ab = cur ? B.bfa : B.bf0;
+  double* Bb = cur ? B.bf0 : B.bfa;
   launch_begin_step(P, b, s);
-  const StageArgs s1 = stage_args(P, B, b, 1, AU, AV, AU, AV, BU, BV, work);
-  const StageArgs s2 = stage_args(P, B, b, 2, AU, AV, BU, BV, B.Ub, B.Vb, work);
-  const StageArgs s3 = stage_args(P, B, b, 3, AU, AV, B.Ub, B.Vb, BU, BV, work);
+  StageArgs s1 = stage_args(P, B, b, 1, AU, AV, AU, AV, BU, BV, work);
+  StageArgs s2 = stage_args(P, B, b, 2, AU, AV, BU, BV, B.Ub, B.Vb, work);
+  StageArgs s3 = stage_args(P, B, b, 3, AU, AV, B.Ub, B.Vb, BU, BV, work);
+  if (ct) {
+    s1.ct = s2.ct = s3.ct = 1;
+    s1.b0 = s2.b0 = s3.b0 = Ab;
+    s1.bs = Ab;
+    s1.bout = Bb;
+    s2.bs = Bb;
+    s2.bout = B.bfb;
+    s3.bs = B.bfb;
+    s3.bout = Bb;
+  }
   for (const StageArgs* a : {&s1, &s2, &s3}) launch_stage(precision, tu, *a, s);
   launch_end_step(b, s);
 }

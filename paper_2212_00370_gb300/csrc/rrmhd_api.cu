@@ -46,6 +46,7 @@ struct rrmhd_ctx {
 namespace {
 
 double* cur_U(const rrmhd_ctx* c) { return c->cur ? c->B.Ua : c->B.U0; }
+double* cur_b(const rrmhd_ctx* c) { return c->cur ? c->B.bfa : c->B.bf0; }
 double* cur_V(const rrmhd_ctx* c) { return c->cur ? c->B.Va : c->B.V0; }
 
 rrmhd_status set_err(const rrmhd_ctx* c, rrmhd_status s, const std::string& msg) {
@@ -145,6 +146,7 @@ void rrmhd_default_opts(rrmhd_opts* o) {
   o->pvm_k = 3;
   o->pvm_products = 0;
   o->solver = RRMHD_SOLVER_PVM;
+  o->ct = 0;
 }
 
 void rrmhd_destroy(rrmhd_ctx* c) {
@@ -157,7 +159,8 @@ void rrmhd_destroy(rrmhd_ctx* c) {
   const rr::DeviceBufs& B = c->B;
   void* bufs[] = {B.inst, B.cell_off, B.face_off, B.U0,  B.Ua,    B.Ub,   B.V0,
                   B.Va,   B.Vb,       B.kappa,    B.sigma, B.Fhat, B.t,    B.t_end,
-                  B.dt,   B.smax,     B.status,   B.bad, B.jc};
+                  B.dt,   B.smax,     B.status,   B.bad, B.jc,   B.edge_off, B.bf0,
+                  B.bfa,  B.bfb,      B.emf};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;
@@ -191,6 +194,11 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
   A(dalloc(c, &B.inst, n_inst));
   A(dalloc(c, &B.cell_off, n_inst + 1));
   A(dalloc(c, &B.face_off, 3 * (size_t)(n_inst + 1)));
+  A(dalloc(c, &B.edge_off, 3 * (size_t)(n_inst + 1)));
+  if (o.ct) {
+    for (double** p : {&B.bf0, &B.bfa, &B.bfb}) A(dalloc(c, p, (size_t)L.nfaces));
+    A(dalloc(c, &B.emf, (size_t)L.nedges));
+  }
   for (double** p : {&B.U0, &B.Ua, &B.Ub, &B.V0, &B.Va, &B.Vb}) A(dalloc(c, p, N12));
   A(dalloc(c, &B.kappa, L.ncells));
   A(dalloc(c, &B.sigma, L.ncells));
@@ -212,6 +220,12 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
     A(cuda_check(c, cudaMemcpyAsync(B.face_off, L.face_off.data(),
                                     sizeof(int64_t) * 3 * (n_inst + 1), cudaMemcpyHostToDevice, st),
                  "upload"));
+    A(cuda_check(c, cudaMemcpyAsync(B.edge_off, L.edge_off.data(),
+                                    sizeof(int64_t) * 3 * (n_inst + 1), cudaMemcpyHostToDevice, st),
+                 "upload"));
+    if (o.ct)
+      for (double* p : {B.bf0, B.bfa, B.bfb})
+        A(cuda_check(c, cudaMemsetAsync(p, 0, sizeof(double) * (L.nfaces ? L.nfaces : 1), st), "memset"));
     std::vector<double> zeros(n_inst, 0.0), inf(n_inst, std::numeric_limits<double>::infinity());
     A(cuda_check(c, cudaMemcpyAsync(B.t, zeros.data(), sizeof(double) * n_inst,
                                     cudaMemcpyHostToDevice, st), "upload"));
@@ -282,11 +296,44 @@ static rrmhd_status refresh_state(rrmhd_ctx* c) {
   return RRMHD_OK;
 }
 
+// Constrained transport: periodic duplicate faces made equal, then the
+// cell-centred B of the current state set to the face means.
+static rrmhd_status ct_sync_cells(rrmhd_ctx* c) {
+  const Batch b = batch_of(c);
+  rr::launch_ct_canonical_f64(b, cur_b(c), c->stream);
+  rr::launch_cells_from_faces_f64(b, cur_b(c), cur_V(c), c->stream);
+  RR_CUDA(c, cudaGetLastError());
+  return RRMHD_OK;
+}
+
 rrmhd_status rrmhd_set_state(rrmhd_ctx* c, const double* V) {
   if (!c || !V) return set_err(c, RRMHD_EINVAL, "null argument");
   RR_CUDA(c, cudaMemcpyAsync(cur_V(c), V, sizeof(double) * 12 * c->L.ncells,
                              cudaMemcpyDeviceToDevice, c->stream));
+  if (c->opts.ct) {
+    rr::launch_faces_from_cells_f64(batch_of(c), cur_V(c), cur_b(c), c->stream);
+    rrmhd_status s = ct_sync_cells(c);
+    if (s != RRMHD_OK) return s;
+  }
   return refresh_state(c);
+}
+
+rrmhd_status rrmhd_set_face_field(rrmhd_ctx* c, const double* b) {
+  if (!c || !b) return set_err(c, RRMHD_EINVAL, "null argument");
+  if (!c->opts.ct) return set_err(c, RRMHD_EINVAL, "constrained transport is off (opts.ct)");
+  RR_CUDA(c, cudaMemcpyAsync(cur_b(c), b, sizeof(double) * c->L.nfaces, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  rrmhd_status s = ct_sync_cells(c);
+  if (s != RRMHD_OK) return s;
+  return refresh_state(c);
+}
+
+rrmhd_status rrmhd_get_face_field(const rrmhd_ctx* c, double* b) {
+  if (!c || !b) return RRMHD_EINVAL;
+  if (!c->opts.ct) return set_err(c, RRMHD_EINVAL, "constrained transport is off (opts.ct)");
+  RR_CUDA(c, cudaMemcpyAsync(b, cur_b(c), sizeof(double) * c->L.nfaces, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  return RRMHD_OK;
 }
 
 rrmhd_status rrmhd_get_state(const rrmhd_ctx* c, double* U, double* V) {
@@ -335,7 +382,8 @@ static rrmhd_status build_step_graph(rrmhd_ctx* c, Lane& L, int cur) {
   if (!c->cap_stream)
     RR_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   RR_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  rr::enqueue_step(c->P, c->opts.precision, c->tune, c->B, L.b, cur, L.work, c->cap_stream);
+  rr::enqueue_step(c->P, c->opts.precision, c->tune, c->B, L.b, cur, L.work, c->cap_stream,
+                   c->opts.ct);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
   if (e != cudaSuccess) {
@@ -408,6 +456,10 @@ rrmhd_status rrmhd_flux_sweep(rrmhd_ctx* c, int dir, double* Fhat) {
   StageArgs a = stage_args(c, b, 0, cur_U(c), cur_V(c), cur_U(c), cur_V(c), nullptr, nullptr);
   a.check_active = 0;
   a.work = batch_work(c);
+  if (c->opts.ct) {
+    a.ct = 1;
+    a.bs = cur_b(c);
+  }
   const int64_t nd = c->L.dir_base[dir + 1] - c->L.dir_base[dir];
   if (c->opts.precision == RRMHD_FP32_BULK) {
     // FP32 fluxes into the context's face buffer, widened into the caller's array
@@ -445,9 +497,23 @@ rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
   double* BU = cur ? c->B.U0 : c->B.Ua;
   double* BV = cur ? c->B.V0 : c->B.Va;
   unsigned long long* w = batch_work(c);
-  const StageArgs st[3] = {rr::stage_args(c->P, c->B, b, 1, AU, AV, AU, AV, BU, BV, w),
-                           rr::stage_args(c->P, c->B, b, 2, AU, AV, BU, BV, c->B.Ub, c->B.Vb, w),
-                           rr::stage_args(c->P, c->B, b, 3, AU, AV, c->B.Ub, c->B.Vb, BU, BV, w)};
+  StageArgs st[3] = {rr::stage_args(c->P, c->B, b, 1, AU, AV, AU, AV, BU, BV, w),
+                     rr::stage_args(c->P, c->B, b, 2, AU, AV, BU, BV, c->B.Ub, c->B.Vb, w),
+                     rr::stage_args(c->P, c->B, b, 3, AU, AV, c->B.Ub, c->B.Vb, BU, BV, w)};
+  if (c->opts.ct) {
+    double* Ab = cur ? c->B.bfa : c->B.bf0;
+    double* Bb = cur ? c->B.bf0 : c->B.bfa;
+    for (StageArgs& x : st) {
+      x.ct = 1;
+      x.b0 = Ab;
+    }
+    st[0].bs = Ab;
+    st[0].bout = Bb;
+    st[1].bs = Bb;
+    st[1].bout = c->B.bfb;
+    st[2].bs = c->B.bfb;
+    st[2].bout = Bb;
+  }
   cudaEvent_t ev[14];
   for (auto& e : ev) RR_CUDA(c, cudaEventCreate(&e));
   cudaStream_t s = c->stream;
@@ -458,6 +524,10 @@ rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
   const int pr = c->opts.precision;
   for (int i = 0; i < 3; ++i) {
     rr::launch_faces(pr, st[i], c->tune.faces, s);
+    if (st[i].ct) {
+      rr::launch_emf_f64(st[i], s);
+      rr::launch_bface_f64(st[i], s);
+    }
     cudaEventRecord(ev[k++], s);
     rr::launch_cells(pr, st[i], c->tune.cells, s);
     cudaEventRecord(ev[k++], s);

@@ -122,6 +122,11 @@ static __device__ __noinline__ void face_item(const StageArgs& a, int64_t t) {
     load12(a.Vs, N, cidx[3], w0);
     reconstruct(a.P.recon, w1, w2, w0, VR, tmp);  // cell f: its left face
   }
+  if (a.ct && I.ndim >= 2) {  // constrained transport: the staggered normal field
+    const double bn = a.bs[g];
+    VL[5 + d] = bn;
+    VR[5 + d] = bn;
+  }
   const double dxd = I.dx[d];
   const double tauL = (__ldg(a.Us + cidx[1]) * (__ldg(a.kappa + cidx[1]) + __ldg(a.sigma + cidx[1]))) * dxd;
   const double tauR = (__ldg(a.Us + cidx[2]) * (__ldg(a.kappa + cidx[2]) + __ldg(a.sigma + cidx[2]))) * dxd;
@@ -183,6 +188,8 @@ __device__ __forceinline__ int cell_update(const StageArgs& a, int64_t c, const 
     else
       Ust[k] = ca * a.U0[k * N + c] + cb * (us - acc);
   }
+  if (a.ct && I.ndim >= 2)  // constrained transport: B_d is the mean of the two faces
+    for (int d = 0; d < I.ndim; ++d) Ust[5 + d] = 0.5 * (a.bout[fl[d]] + a.bout[fr[d]]);
   double vs[NV];
   load12(a.Vs, N, c, vs);
   const double Zg = prim_Z(a.P, vs);
@@ -265,8 +272,10 @@ __global__ void __launch_bounds__(kFaceThreads) k_fallback_faces(StageArgs a) {
   load12(a.Vs, b.ncells, cl, vl);
   load12(a.Vs, b.ncells, cr, vr);
   llf_flux(a.P, d, vl, vr, F);
+  const bool keep_b = a.ct && I.ndim >= 2;  // CT: the solver's magnetic fluxes stay
 #pragma unroll
-  for (int k = 0; k < NV; ++k) a.Fhat[k * a.fstride + g] = F[k];
+  for (int k = 0; k < NV; ++k)
+    if (!keep_b || k < 5 || k > 7) a.Fhat[k * a.fstride + g] = F[k];
 }
 
 // Admissibility fallback, cells: update again every cell with a changed face
@@ -316,6 +325,142 @@ __global__ void __launch_bounds__(kCellThreads, RR_CELL_MIN_BLOCKS) k_fallback_c
     double s = signal_speed(a.P, 0, Vn) / I.dx[0];
     for (int d = 1; d < I.ndim; ++d) s = s + signal_speed(a.P, d, Vn) / I.dx[d];
     atomicMax(b.st.smax + q.i, (unsigned long long)__double_as_longlong(s));
+  }
+}
+
+// ------------------------------------------------------------ constrained transport
+// CT-contact edge EMF (Gardiner & Stone 2005, Eqs. 41 and 50), E_e at the edge
+// between cells (ia-1, ia) along a and (ib-1, ib) along b, e = a x b cyclic:
+// the mean of the four face EMFs (-F^a(B_b) at a-faces, +F^b(B_a) at b-faces)
+// plus the half-cell differences to the cell-centre E_ref = v_b B_a - v_a B_b,
+// each taken from the side the face mass flux comes from.
+__device__ __forceinline__ double ct_upwind(double f, double lo, double hi) {
+  if (f > 0.0) return lo;
+  if (f < 0.0) return hi;
+  return 0.5 * (lo + hi);
+}
+
+__global__ void __launch_bounds__(kFaceThreads) k_emf(StageArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Batch& b = a.b;
+  if (t >= lane_edges(b)) return;
+  const EdgePos q = edge_pos(b, t);
+  if (!inst_active(b, q.i)) return;
+  const InstDesc& I = q.I;
+  const int A = (q.e + 1) % 3, Bd = (q.e + 2) % 3;
+  int pa0[3] = {q.pos[0], q.pos[1], q.pos[2]}, pa1[3] = {q.pos[0], q.pos[1], q.pos[2]};
+  pa0[Bd] -= 1;
+  const int64_t fa0 = face_gidx(b, I, A, pa0), fa1 = face_gidx(b, I, A, pa1);
+  int pb0[3] = {q.pos[0], q.pos[1], q.pos[2]}, pb1[3] = {q.pos[0], q.pos[1], q.pos[2]};
+  pb0[A] -= 1;
+  const int64_t fb0 = face_gidx(b, I, Bd, pb0), fb1 = face_gidx(b, I, Bd, pb1);
+  const int64_t FS = a.fstride;
+  const double Ea0 = -a.Fhat[(5 + Bd) * FS + fa0], Ea1 = -a.Fhat[(5 + Bd) * FS + fa1];
+  const double Eb0 = a.Fhat[(5 + A) * FS + fb0], Eb1 = a.Fhat[(5 + A) * FS + fb1];
+  const double ma0 = a.Fhat[fa0], ma1 = a.Fhat[fa1];
+  const double mb0 = a.Fhat[fb0], mb1 = a.Fhat[fb1];
+  const int64_t N = b.ncells;
+  double Er[2][2];
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      int p[3] = {q.pos[0], q.pos[1], q.pos[2]};
+      p[A] += s - 1;
+      p[Bd] += r - 1;
+      const int64_t c = cell_gidx(I, p);
+      const double va = a.Vs[(1 + A) * N + c], vb = a.Vs[(1 + Bd) * N + c];
+      const double Ba = a.Vs[(5 + A) * N + c], Bb = a.Vs[(5 + Bd) * N + c];
+      Er[s][r] = vb * Ba - va * Bb;
+    }
+  const double Lb = ct_upwind(ma0, Eb0 - Er[0][0], Eb1 - Er[1][0]);
+  const double Ub = ct_upwind(ma1, Er[0][1] - Eb0, Er[1][1] - Eb1);
+  const double La = ct_upwind(mb0, Ea0 - Er[0][0], Ea1 - Er[0][1]);
+  const double Ra = ct_upwind(mb1, Er[1][0] - Ea0, Er[1][1] - Ea1);
+  a.emf[q.g] = 0.25 * (((Ea0 + Ea1) + Eb0) + Eb1) + 0.25 * (Lb - Ub) + 0.25 * (La - Ra);
+}
+
+// Face-field stage update: b_out = a b0 + c (b_s - dt (curl E)_d), with
+// (curl E)_d = dE_{d+2}/dx_{d+1} - dE_{d+1}/dx_{d+2} (cyclic) and the stage weights of
+// U.  An inactive instance carries its step-start field in stage 3.
+__global__ void __launch_bounds__(kFaceThreads) k_bface(StageArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Batch& b = a.b;
+  if (t >= lane_faces(b)) return;
+  const int64_t g = lane_face(b, t);
+  const FacePos fp = face_pos(b, g);
+  const InstDesc& I = fp.I;
+  if (I.ndim < 2) return;
+  if (!inst_active(b, fp.i)) {
+    if (a.stage == 3) a.bout[g] = a.b0[g];
+    return;
+  }
+  const int d = fp.d, p1 = (d + 1) % 3, p2 = (d + 2) % 3;
+  const double dt = b.st.dt[fp.i];
+  double curl = 0.0;
+  if (has_edges(I, p2)) {
+    int q0[3] = {fp.pos[0], fp.pos[1], fp.pos[2]}, q1[3] = {fp.pos[0], fp.pos[1], fp.pos[2]};
+    q1[p1] += 1;
+    curl = curl + (a.emf[edge_gidx(b, I, p2, q1)] - a.emf[edge_gidx(b, I, p2, q0)]) / I.dx[p1];
+  }
+  if (has_edges(I, p1)) {
+    int q0[3] = {fp.pos[0], fp.pos[1], fp.pos[2]}, q1[3] = {fp.pos[0], fp.pos[1], fp.pos[2]};
+    q1[p2] += 1;
+    curl = curl - (a.emf[edge_gidx(b, I, p1, q1)] - a.emf[edge_gidx(b, I, p1, q0)]) / I.dx[p2];
+  }
+  double ca = 0.0, cb = 1.0;
+  if (a.stage == 2) {
+    ca = 0.75;
+    cb = 0.25;
+  } else if (a.stage == 3) {
+    ca = 1.0 / 3.0;
+    cb = 2.0 / 3.0;
+  }
+  const double upd = a.bs[g] - dt * curl;
+  a.bout[g] = (a.stage == 1) ? upd : ca * a.b0[g] + cb * upd;
+}
+
+// Set-up: face field from cell-centred B (mean of the two cells next to a face).
+__global__ void k_faces_from_cells(Batch b, const double* __restrict__ V, double* bface) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= lane_faces(b)) return;
+  const int64_t g = lane_face(b, t);
+  const FacePos fp = face_pos(b, g);
+  const InstDesc& I = fp.I;
+  if (I.ndim < 2) return;
+  int pl[3] = {fp.pos[0], fp.pos[1], fp.pos[2]}, pr[3] = {fp.pos[0], fp.pos[1], fp.pos[2]};
+  pl[fp.d] -= 1;
+  const int64_t N = b.ncells;
+  const double bl = V[(5 + fp.d) * N + cell_gidx(I, pl)];
+  const double br = V[(5 + fp.d) * N + cell_gidx(I, pr)];
+  bface[g] = 0.5 * (bl + br);
+}
+
+// Set-up: periodic duplicate faces (index n_d) take the value of face 0.
+__global__ void k_ct_canonical(Batch b, double* bface) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= lane_faces(b)) return;
+  const int64_t g = lane_face(b, t);
+  const FacePos fp = face_pos(b, g);
+  const InstDesc& I = fp.I;
+  if (I.ndim < 2 || I.bc[fp.d] != 1 || fp.pos[fp.d] != I.n[fp.d]) return;
+  int p[3] = {fp.pos[0], fp.pos[1], fp.pos[2]};
+  p[fp.d] = 0;
+  bface[g] = bface[face_gidx(b, I, fp.d, p)];
+}
+
+// Set-up: cell-centred B_d (d < ndim) of V from the face means.
+__global__ void k_cells_from_faces(Batch b, const double* __restrict__ bface, double* V) {
+  const int64_t c = b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= b.c_end) return;
+  const CellPos q = cell_pos(b, c);
+  const InstDesc& I = q.I;
+  if (I.ndim < 2) return;
+  const int64_t N = b.ncells;
+  for (int d = 0; d < I.ndim; ++d) {
+    int pl[3] = {q.p[0], q.p[1], q.p[2]}, pr[3] = {q.p[0], q.p[1], q.p[2]};
+    pr[d] += 1;
+    V[(5 + d) * N + c] = 0.5 * (bface[face_gidx(b, I, d, pl)] + bface[face_gidx(b, I, d, pr)]);
   }
 }
 
@@ -484,6 +629,31 @@ void launch_fallback_f64(const StageArgs& a, cudaStream_t s) {
   const int64_t nc = a.b.c_end - a.b.c_begin;
   if (nf > 0) k_fallback_faces<<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(a);
   if (nc > 0) k_fallback_cells<<<grid_for(nc, kCellThreads), kCellThreads, 0, s>>>(a);
+}
+
+void launch_emf_f64(const StageArgs& a, cudaStream_t s) {
+  const int64_t n = a.b.e_count[0] + a.b.e_count[1] + a.b.e_count[2];
+  if (n > 0) k_emf<<<grid_for(n, kFaceThreads), kFaceThreads, 0, s>>>(a);
+}
+
+void launch_bface_f64(const StageArgs& a, cudaStream_t s) {
+  const int64_t n = a.b.f_count[0] + a.b.f_count[1] + a.b.f_count[2];
+  if (n > 0) k_bface<<<grid_for(n, kFaceThreads), kFaceThreads, 0, s>>>(a);
+}
+
+void launch_faces_from_cells_f64(const Batch& b, const double* V, double* bface, cudaStream_t s) {
+  const int64_t n = b.f_count[0] + b.f_count[1] + b.f_count[2];
+  if (n > 0) k_faces_from_cells<<<grid_for(n, 128), 128, 0, s>>>(b, V, bface);
+}
+
+void launch_ct_canonical_f64(const Batch& b, double* bface, cudaStream_t s) {
+  const int64_t n = b.f_count[0] + b.f_count[1] + b.f_count[2];
+  if (n > 0) k_ct_canonical<<<grid_for(n, 128), 128, 0, s>>>(b, bface);
+}
+
+void launch_cells_from_faces_f64(const Batch& b, const double* bface, double* V, cudaStream_t s) {
+  const int64_t n = b.c_end - b.c_begin;
+  if (n > 0) k_cells_from_faces<<<grid_for(n, 128), 128, 0, s>>>(b, bface, V);
 }
 
 void launch_signal_f64(const Params& P, const Batch& b, const double* V, cudaStream_t s) {

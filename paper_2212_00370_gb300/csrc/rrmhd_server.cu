@@ -479,7 +479,7 @@ rrmhd_status rrmhd_server_create(const rrmhd_opts* opts, const rrmhd_server_conf
                                  rrmhd_server** out) {
   if (!out) return RRMHD_EINVAL;
   *out = nullptr;
-  if (!opts || !rr::opts_ok(*opts)) return RRMHD_EINVAL;
+  if (!opts || !rr::opts_ok(*opts) || opts->ct) return RRMHD_EINVAL;  // no face field in the server
   rrmhd_server_config c{};
   if (cfg) c = *cfg;
   if (c.mem_bytes < 0 || c.max_resident_cells < 0 || c.max_resident < 0) return RRMHD_EINVAL;

@@ -32,7 +32,7 @@ class rrmhd_opts(C.Structure):
                 ("pvm_eps", C.c_double), ("recon", C.c_int), ("beta_mode", C.c_int),
                 ("precision", C.c_int), ("c2p_maxit", C.c_int), ("imp_maxit", C.c_int),
                 ("imp_tol", C.c_double), ("lanes", C.c_int), ("pvm_k", C.c_int),
-                ("pvm_products", C.c_int), ("solver", C.c_int)]
+                ("pvm_products", C.c_int), ("solver", C.c_int), ("ct", C.c_int)]
 
 
 class rrmhd_tuning(C.Structure):
@@ -107,6 +107,8 @@ _SIGNATURES = [
     ("rrmhd_get_tuning", C.c_int, [_VP, C.POINTER(rrmhd_tuning)]),
     ("rrmhd_set_tuning", C.c_int, [_VP, C.POINTER(rrmhd_tuning)]),
     ("rrmhd_autotune", C.c_int, [_VP, C.c_int, C.POINTER(rrmhd_tuning), _DP]),
+    ("rrmhd_set_face_field", C.c_int, [_VP, _VP]),
+    ("rrmhd_get_face_field", C.c_int, [_VP, _VP]),
     ("rrmhd_cfl_dt_noalloc", C.c_int, [C.POINTER(rrmhd_grid), C.POINTER(rrmhd_opts), _VP, _VP, _VP]),
     ("rrmhd_server_create", C.c_int, [C.POINTER(rrmhd_opts), C.POINTER(rrmhd_server_config),
                                       C.POINTER(_VP)]),
@@ -272,6 +274,18 @@ class Context:
 
     def launches_per_step(self):
         return lib().rrmhd_launches_per_step(self.ctx)
+
+    def num_face_field(self):
+        return sum(self.num_faces(d) for d in range(3))
+
+    def set_face_field(self, b):
+        self._b_in = b.contiguous()
+        _check(self.ctx, lib().rrmhd_set_face_field(self.ctx, _ptr(self._b_in)))
+
+    def get_face_field(self):
+        b = self._t(self.num_face_field())
+        _check(self.ctx, lib().rrmhd_get_face_field(self.ctx, _ptr(b)))
+        return b
 
     def get_tuning(self):
         t = rrmhd_tuning()

@@ -82,6 +82,7 @@ def setup(shape, seed):
     V, kappa, sigma = smooth_state(shape, seed)
     b = curl_faces(shape)
     assert b.size == O.ct_nfaces(g)
+    O.ct_canonical(g, b)
     U = O.prim2con(V, P)
     O.ct_cells_from_faces(g, b, U, V)
     U = O.prim2con(V, P)
