@@ -323,6 +323,45 @@ def measure_variant(a, opts, tuning, steps=5):
             "failed_instances": int((~live).sum()), "launches": launches}
 
 
+VARS = ["D", "Sx", "Sy", "Sz", "tau", "Bx", "By", "Bz", "E", "Fx", "Fy", "Fz"]
+
+
+def measure_accuracy(a, n_inst=256, steps=5):
+    """Per-variable relative L1 of the FP32-bulk form against the FP64 form (which is
+    bit-identical to the oracle) on an evenly spaced sample of the C1 batch after
+    `steps` steps; instances that fail in either form are left out."""
+    import torch
+
+    from paper_2212_00370_gb300 import rrmhd
+    from paper_2212_00370_gb300 import workloads as W
+
+    w = W.riemann_batch(a.instances, seed=W.SEED_BASE + 1)
+    w = w.subset(list(np.linspace(0, w.n_inst - 1, n_inst).astype(int)))
+    grids = [rrmhd.make_grid(1, g["n"], g["dx"], g["bc"]) for g in w.grids]
+    out = {}
+    for prec in ("fp32_bulk", "fp64"):
+        ctx = rrmhd.Context(grids, gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl, precision=prec)
+        ctx.set_opacity(torch.tensor(w.kappa, device="cuda"), torch.tensor(w.sigma, device="cuda"))
+        ctx.set_state(torch.tensor(w.V, device="cuda"))
+        ctx.set_times(np.zeros(w.n_inst), np.full(w.n_inst, np.inf))
+        ctx.imex_step(steps)
+        out[prec] = (ctx.get_state()[0].cpu().numpy(), ctx.inst_status())
+        ctx.close()
+    (U32, s32), (U64, s64) = out["fp32_bulk"], out["fp64"]
+    off = w.cell_offsets()
+    keep = np.zeros(w.ncells, dtype=bool)
+    for i in np.nonzero((s32 == 0) & (s64 == 0))[0]:
+        keep[off[i]:off[i + 1]] = True
+    l1 = {}
+    for k in range(12):
+        den = np.abs(U64[k, keep]).sum()
+        if den > 0:
+            l1[VARS[k]] = float(np.abs(U32[k, keep] - U64[k, keep]).sum() / den)
+    return {"rel_l1_vs_fp64": l1, "max": max(l1.values()), "instances": int(n_inst),
+            "compared": int(((s32 == 0) & (s64 == 0)).sum()), "steps": steps,
+            "note": "FP64 form = the oracle bit for bit; bound 1e-5 per variable"}
+
+
 def measure_serving(a, tuning=None):
     """C4 serving sample: the first `serve_requests` requests of the C4 arrival process
     (Poisson, 200 requests/s; 70 % 1D N~U{256..4096}, 30 % planar 2D side~U{128..512};
@@ -425,6 +464,7 @@ def run_ours(a, rank, world, pool, cores):
                        "p99_ms": f["p99_ms"], "roofline": f["roofline"], "e2e": f["e2e"],
                        "failed_instances": f["failed"], "clocks": f["clocks"]}
         out["fp32_bulk_speedup_over_fp64"] = head["value"] / f["value"]
+        out["fp32_bulk_accuracy"] = measure_accuracy(a)
         out["gpu_launches"] += f["gpu_launches"]
         g = res["fp64_tangent"]
         out["fp64_tangent"] = {"value": g["value"], "ms_per_step": g["ms_per_step"], "p50_ms": g["p50_ms"],

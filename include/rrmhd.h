@@ -165,9 +165,12 @@ rrmhd_status rrmhd_get_inst_status(const rrmhd_ctx* ctx, int32_t* status);
 rrmhd_status rrmhd_imex_step(rrmhd_ctx* ctx, int nsteps);
 
 /* Same as rrmhd_imex_step, from and to HOST buffers: copies V_in (host
- * double[12][ncells], pinned memory recommended) to the device, sets it as the
- * state, takes nsteps steps and copies the primitives back to V_out (host).
- * Synchronous. */
+ * double[12][ncells], pinned memory recommended) to the device, takes nsteps steps
+ * and copies the primitives back to V_out (host).  Synchronous.  If V_in equals
+ * the context's current primitives bit for bit (a run that continues from the last
+ * V_out), the run continues exactly as rrmhd_imex_step would: the per-cell
+ * implicit-solver history, statuses and CFL speeds are kept.  Otherwise V_in becomes
+ * the state as with rrmhd_set_state. */
 rrmhd_status rrmhd_imex_step_host(rrmhd_ctx* ctx, const double* V_in, double* V_out, int nsteps);
 
 /* Pointwise Eq. eqU on caller buffers: V, U double[12][n]. */

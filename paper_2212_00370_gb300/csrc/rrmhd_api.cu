@@ -28,6 +28,17 @@ struct Lane {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per value of rrmhd_ctx::cur
 };
 
+// Sets *flag when the two arrays differ in any bit (host-buffer entry: is the
+// incoming state the context's own?).
+__global__ void k_differs(const unsigned long long* __restrict__ a,
+                          const unsigned long long* __restrict__ b, int64_t n, int* flag) {
+  int diff = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    diff |= (a[i] != b[i]);
+  if (__syncthreads_or(diff) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
 struct rrmhd_ctx {
   rrmhd_opts opts;
   Params P;
@@ -40,6 +51,8 @@ struct rrmhd_ctx {
   unsigned long long* work = nullptr; // chunk counters: 2 per lane, then 2 for whole-batch calls
   std::vector<Lane> lanes;
   cudaEvent_t fork = nullptr;
+  int* d_flag = nullptr;  // one device int (host-buffer entry)
+  int* h_flag = nullptr;  // pinned mirror
   std::string err;
 };
 
@@ -156,6 +169,8 @@ void rrmhd_destroy(rrmhd_ctx* c) {
   destroy_lanes(c);
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->d_flag) cudaFree(c->d_flag);
+  if (c->h_flag) cudaFreeHost(c->h_flag);
   const rr::DeviceBufs& B = c->B;
   void* bufs[] = {B.inst, B.cell_off, B.face_off, B.U0,  B.Ua,    B.Ub,   B.V0,
                   B.Va,   B.Vb,       B.kappa,    B.sigma, B.Fhat, B.t,    B.t_end,
@@ -195,6 +210,8 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
   A(dalloc(c, &B.cell_off, n_inst + 1));
   A(dalloc(c, &B.face_off, 3 * (size_t)(n_inst + 1)));
   A(dalloc(c, &B.edge_off, 3 * (size_t)(n_inst + 1)));
+  A(dalloc(c, &c->d_flag, 1));
+  A(cuda_check(c, cudaMallocHost((void**)&c->h_flag, sizeof(int)), "cudaMallocHost"));
   if (o.ct) {
     for (double** p : {&B.bf0, &B.bfa, &B.bfb}) A(dalloc(c, p, (size_t)L.nfaces));
     A(dalloc(c, &B.emf, (size_t)L.nedges));
@@ -416,10 +433,23 @@ rrmhd_status rrmhd_imex_step(rrmhd_ctx* c, int nsteps) {
 
 rrmhd_status rrmhd_imex_step_host(rrmhd_ctx* c, const double* V_in, double* V_out, int nsteps) {
   if (!c || !V_in || !V_out || nsteps < 0) return set_err(c, RRMHD_EINVAL, "bad argument");
-  const size_t bytes = sizeof(double) * 12 * c->L.ncells;
-  RR_CUDA(c, cudaMemcpyAsync(cur_V(c), V_in, bytes, cudaMemcpyHostToDevice, c->stream));
-  rrmhd_status s = refresh_state(c);
-  if (s != RRMHD_OK) return s;
+  const int64_t n = (int64_t)12 * c->L.ncells;
+  const size_t bytes = sizeof(double) * n;
+  // V_in to the scratch set, then: the context's own state (a continuing run) or a new one?
+  RR_CUDA(c, cudaMemcpyAsync(c->B.Vb, V_in, bytes, cudaMemcpyHostToDevice, c->stream));
+  RR_CUDA(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  k_differs<<<1216, 256, 0, c->stream>>>(reinterpret_cast<const unsigned long long*>(c->B.Vb),
+                                         reinterpret_cast<const unsigned long long*>(cur_V(c)), n,
+                                         c->d_flag);
+  RR_CUDA(c, cudaGetLastError());
+  RR_CUDA(c, cudaMemcpyAsync(c->h_flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  RR_CUDA(c, cudaStreamSynchronize(c->stream));
+  rrmhd_status s = RRMHD_OK;
+  if (*c->h_flag) {  // a new state: as rrmhd_set_state
+    RR_CUDA(c, cudaMemcpyAsync(cur_V(c), c->B.Vb, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    s = refresh_state(c);
+    if (s != RRMHD_OK) return s;
+  }
   s = rrmhd_imex_step(c, nsteps);
   if (s != RRMHD_OK) return s;
   RR_CUDA(c, cudaMemcpyAsync(V_out, cur_V(c), bytes, cudaMemcpyDeviceToHost, c->stream));

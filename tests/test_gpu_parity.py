@@ -220,3 +220,27 @@ def test_invalid_arguments():
     assert e.value.code == 10
     with pytest.raises(rrmhd.RRMHDError):
         rrmhd.Context([rrmhd.make_grid(1, (8,), (0.1,))], gamma=1.0)
+
+
+def test_host_buffer_entry_continues_and_restarts_bitwise():
+    """rrmhd_imex_step_host: a run fed its own previous output continues exactly as
+    the device path; any other input restarts from it like set_state."""
+    w = W.riemann_batch(30, seed=19, nmin=20, nmax=200)
+    ref = gpu_context(w)
+    ref.imex_step(4)
+    Vref = ref.get_state()[1].cpu().numpy()
+    ctx = gpu_context(w)
+    h_in = np.ascontiguousarray(w.V.copy())
+    h_out = np.empty_like(h_in)
+    for _ in range(4):
+        ctx.imex_step_host(h_in, h_out, 1)
+        h_in, h_out = h_out.copy(), h_in
+    compare_bitwise(h_in, Vref, "continuing host-buffer run")
+    # another state on the same grids restarts from it, as a fresh context would
+    V2 = np.ascontiguousarray(w.V.copy())
+    V2[0] *= 1.01
+    ctx.imex_step_host(V2, h_out, 2)
+    w2 = W.Workload("restart", w.grids, V2, w.kappa, w.sigma, w.t_end, w.gamma)
+    fresh = gpu_context(w2)
+    fresh.imex_step(2)
+    compare_bitwise(h_out, fresh.get_state()[1].cpu().numpy(), "restarted host-buffer run")
