@@ -176,6 +176,20 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def aggregate_over_ranks(t_s, zones, world):
+    """Whole-job figures of replicas: the slowest rank's time and the zone-updates
+    of all ranks (no data-path collective; this is the one reduction)."""
+    if world <= 1:
+        return t_s, zones
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_s, zones], dtype=torch.float64)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(tt[1])
+
+
 def measure(a, precision, rank, world, local):
     """Time K steps of the C1 batch in one precision; returns a dict of measurements."""
     import torch
@@ -227,13 +241,7 @@ def measure(a, precision, rank, world, local):
     st_after = ctx.inst_status()
     live = (st_before == 0) & (st_after == 0)
     zones = float(n_cells[live].sum()) * a.steps
-    t_s = total_ms / 1e3
-    if world > 1:
-        tt = torch.tensor([t_s, zones], dtype=torch.float64)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_s, zones = float(mx[0]), float(tt[1])
+    t_s, zones = aggregate_over_ranks(total_ms / 1e3, zones, world)
     value = zones / t_s
 
     # per-launch-group device times of two more steps (same kernels, whole-batch launches)
