@@ -98,7 +98,8 @@ typedef struct {
                           (CT-contact EMFs of Gardiner & Stone 2005, the scheme the paper's
                           multi-D runs use, Sec. 4): the normal field lives on the faces,
                           cell-centred B is the mean of the two faces, and the discrete
-                          divergence is kept to round-off.  FP64 only.  0: cell-centred B
+                          divergence is kept to round-off.  In the FP32-bulk form the EMFs
+                          are formed in FP64 from the FP32 fluxes.  0: cell-centred B
                           updated by its fluxes (default).                               */
 } rrmhd_opts;
 
@@ -239,10 +240,10 @@ rrmhd_status rrmhd_set_tuning(rrmhd_ctx* ctx, const rrmhd_tuning* t);
 /* Chooses the shapes for this context's batch by timing real steps from its
  * current state: coordinate descent over the cell shapes, then the face shapes,
  * then the lane count; each candidate is timed over `repeats` steps (CUDA events
- * on the context's stream, median), each taken from the same saved state.  The
+ * on the context's stream, the fastest counts), each taken from the same saved state.  The
  * state, times and statuses are restored afterwards, so the context continues as
  * if no step had been taken; the fastest shapes are kept.  best (host, may be
- * NULL) receives them, best_ms (host, may be NULL) the median step time.  Allocates
+ * NULL) receives them, best_ms (host, may be NULL) their best step time.  Allocates
  * a copy of the state for the duration of the call (ENOMEM if that fails). */
 rrmhd_status rrmhd_autotune(rrmhd_ctx* ctx, int repeats, rrmhd_tuning* best, double* best_ms);
 

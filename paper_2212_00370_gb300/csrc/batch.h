@@ -83,6 +83,7 @@ struct StageArgs {
   // field per face (one value per face, the face layout) at the step start (b0),
   // the stage input (bs) and output (bout); the edge EMFs of the stage.
   int ct;
+  int fp32_fluxes;  // the face fluxes are the FP32 ones (FP32-bulk form)
   const double* b0;
   const double* bs;
   double* bout;

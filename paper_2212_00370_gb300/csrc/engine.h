@@ -42,7 +42,7 @@ inline bool opts_ok(const rrmhd_opts& o) {
          (o.precision == RRMHD_FP64 || o.precision == RRMHD_FP32_BULK) && o.lanes >= 1 &&
          (o.pvm_k == 3 || o.pvm_k == 4) && (o.pvm_products == 0 || o.pvm_products == 1) &&
          (o.solver == RRMHD_SOLVER_PVM || o.solver == RRMHD_SOLVER_RADHLL) &&
-         (o.ct == 0 || (o.ct == 1 && o.precision == RRMHD_FP64));
+         (o.ct == 0 || o.ct == 1);
 }
 
 inline bool grid_ok(const rrmhd_grid& g, std::string& why) {
@@ -248,6 +248,7 @@ inline StageArgs stage_args(const Params& P, const DeviceBufs& B, const Batch& b
   a.jc = B.jc;
   a.work = work;
   a.ct = 0;
+  a.fp32_fluxes = 0;
   a.b0 = a.bs = nullptr;
   a.bout = nullptr;
   a.emf = B.emf;
@@ -316,6 +317,7 @@ inline void enqueue_step(const Params& P, int precision, const Tuning& tu, const
   StageArgs s3 = stage_args(P, B, b, 3, AU, AV, B.Ub, B.Vb, BU, BV, work);
   if (ct) {
     s1.ct = s2.ct = s3.ct = 1;
+    s1.fp32_fluxes = s2.fp32_fluxes = s3.fp32_fluxes = (precision == RRMHD_FP32_BULK);
     s1.b0 = s2.b0 = s3.b0 = Ab;
     s1.bs = Ab;
     s1.bout = Bb;

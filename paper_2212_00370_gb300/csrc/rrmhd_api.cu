@@ -488,6 +488,7 @@ rrmhd_status rrmhd_flux_sweep(rrmhd_ctx* c, int dir, double* Fhat) {
   a.work = batch_work(c);
   if (c->opts.ct) {
     a.ct = 1;
+    a.fp32_fluxes = c->opts.precision == RRMHD_FP32_BULK;
     a.bs = cur_b(c);
   }
   const int64_t nd = c->L.dir_base[dir + 1] - c->L.dir_base[dir];
@@ -535,6 +536,7 @@ rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
     double* Bb = cur ? c->B.bf0 : c->B.bfa;
     for (StageArgs& x : st) {
       x.ct = 1;
+      x.fp32_fluxes = c->opts.precision == RRMHD_FP32_BULK;
       x.b0 = Ab;
     }
     st[0].bs = Ab;
@@ -666,7 +668,8 @@ rrmhd_status rrmhd_autotune(rrmhd_ctx* c, int repeats, rrmhd_tuning* best, doubl
     return cudaSuccess;
   };
   rrmhd_status rc = cuda_check(c, copy_state(true), "autotune save");
-  // median step time (ms) of a candidate, each step from the saved state
+  // best step time (ms) of a candidate over `repeats` steps, each from the saved state
+  // (the fastest repeat is the least disturbed by other work on the device)
   auto trial = [&](const rrmhd_tuning& cand, double& ms) -> rrmhd_status {
     rrmhd_status r = rrmhd_set_tuning(c, &cand);
     if (r != RRMHD_OK) return r;
@@ -685,8 +688,7 @@ rrmhd_status rrmhd_autotune(rrmhd_ctx* c, int repeats, rrmhd_tuning* best, doubl
       RR_CUDA(c, cudaEventElapsedTime(&x, e0, e1));
       v.push_back(x);
     }
-    std::sort(v.begin(), v.end());
-    ms = v[v.size() / 2];
+    ms = *std::min_element(v.begin(), v.end());
     return RRMHD_OK;
   };
   rrmhd_tuning cur_best = tuning_to(c->tune, c->opts.lanes);

@@ -68,6 +68,11 @@ static __device__ __noinline__ void face_item_f32(const StageArgs& a, int64_t t)
     rrt::reconstruct<float>(P.recon, w1, w2, w0, VR, tmp);
   }
   const float dxd = (float)I.dx[d];
+  if (a.ct && I.ndim >= 2) {  // constrained transport: the staggered normal field
+    const float bn = (float)a.bs[g];
+    VL[5 + d] = bn;
+    VR[5 + d] = bn;
+  }
   const float tauL = (float)(__ldg(a.Us + cidx[1]) * (__ldg(a.kappa + cidx[1]) + __ldg(a.sigma + cidx[1]))) * dxd;
   const float tauR = (float)(__ldg(a.Us + cidx[2]) * (__ldg(a.kappa + cidx[2]) + __ldg(a.sigma + cidx[2]))) * dxd;
   float F[NV];
@@ -120,6 +125,8 @@ __device__ __forceinline__ int cell_update_f32(const StageArgs& a, int64_t c, co
     const double us = a.Us[k * N + c];
     Ust[k] = (a.stage == 1) ? us - (double)acc : ca * a.U0[k * N + c] + cb * (us - (double)acc);
   }
+  if (a.ct && I.ndim >= 2)  // constrained transport: B_d is the mean of the two faces (FP64)
+    for (int d = 0; d < I.ndim; ++d) Ust[5 + d] = 0.5 * (a.bout[fl[d]] + a.bout[fr[d]]);
   double vs[NV];
   load12(a.Vs, N, c, vs);
   double jc[17];
@@ -197,8 +204,10 @@ __global__ void __launch_bounds__(kFaceThreads) k_fallback_faces_f32(StageArgs a
   load12f(a.Vs, b.ncells, cl, vl);
   load12f(a.Vs, b.ncells, cr, vr);
   rrt::llf_flux<float>(p32_of(a.P), d, vl, vr, F);
+  const bool keep_b = a.ct && I.ndim >= 2;  // CT: the solver's magnetic fluxes stay
 #pragma unroll
-  for (int k = 0; k < NV; ++k) a.Fhat32[k * a.fstride + g] = F[k];
+  for (int k = 0; k < NV; ++k)
+    if (!keep_b || k < 5 || k > 7) a.Fhat32[k * a.fstride + g] = F[k];
 }
 
 __global__ void __launch_bounds__(kCellThreads) k_fallback_cells_f32(StageArgs a) {

@@ -340,6 +340,18 @@ __device__ __forceinline__ double ct_upwind(double f, double lo, double hi) {
   return 0.5 * (lo + hi);
 }
 
+template <class FT>
+__device__ __forceinline__ double fhat(const StageArgs& a, int64_t i);
+template <>
+__device__ __forceinline__ double fhat<double>(const StageArgs& a, int64_t i) { return a.Fhat[i]; }
+template <>
+__device__ __forceinline__ double fhat<float>(const StageArgs& a, int64_t i) {
+  return (double)a.Fhat32[i];
+}
+
+// FT: the precision the face fluxes are stored in (FP64, or FP32 in FP32-bulk);
+// the EMFs and the face field are FP64 either way.
+template <class FT>
 __global__ void __launch_bounds__(kFaceThreads) k_emf(StageArgs a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const Batch& b = a.b;
@@ -355,10 +367,10 @@ __global__ void __launch_bounds__(kFaceThreads) k_emf(StageArgs a) {
   pb0[A] -= 1;
   const int64_t fb0 = face_gidx(b, I, Bd, pb0), fb1 = face_gidx(b, I, Bd, pb1);
   const int64_t FS = a.fstride;
-  const double Ea0 = -a.Fhat[(5 + Bd) * FS + fa0], Ea1 = -a.Fhat[(5 + Bd) * FS + fa1];
-  const double Eb0 = a.Fhat[(5 + A) * FS + fb0], Eb1 = a.Fhat[(5 + A) * FS + fb1];
-  const double ma0 = a.Fhat[fa0], ma1 = a.Fhat[fa1];
-  const double mb0 = a.Fhat[fb0], mb1 = a.Fhat[fb1];
+  const double Ea0 = -fhat<FT>(a, (5 + Bd) * FS + fa0), Ea1 = -fhat<FT>(a, (5 + Bd) * FS + fa1);
+  const double Eb0 = fhat<FT>(a, (5 + A) * FS + fb0), Eb1 = fhat<FT>(a, (5 + A) * FS + fb1);
+  const double ma0 = fhat<FT>(a, fa0), ma1 = fhat<FT>(a, fa1);
+  const double mb0 = fhat<FT>(a, fb0), mb1 = fhat<FT>(a, fb1);
   const int64_t N = b.ncells;
   double Er[2][2];
 #pragma unroll
@@ -633,7 +645,11 @@ void launch_fallback_f64(const StageArgs& a, cudaStream_t s) {
 
 void launch_emf_f64(const StageArgs& a, cudaStream_t s) {
   const int64_t n = a.b.e_count[0] + a.b.e_count[1] + a.b.e_count[2];
-  if (n > 0) k_emf<<<grid_for(n, kFaceThreads), kFaceThreads, 0, s>>>(a);
+  if (n <= 0) return;
+  if (a.fp32_fluxes)
+    k_emf<float><<<grid_for(n, kFaceThreads), kFaceThreads, 0, s>>>(a);
+  else
+    k_emf<double><<<grid_for(n, kFaceThreads), kFaceThreads, 0, s>>>(a);
 }
 
 void launch_bface_f64(const StageArgs& a, cudaStream_t s) {

@@ -152,12 +152,32 @@ def test_ct_radhll_bitwise():
     check([instance((16, 18), 6)], 3, solver="radhll")
 
 
-def test_ct_needs_fp64_and_the_option():
+def test_ct_fp32_bulk_tracks_the_oracle():
+    """FP32-bulk with CT: FP32 face fluxes, FP64 EMFs and face field.  Per-variable
+    relative L1 against the FP64 oracle <= 1e-5; the divergence is kept."""
+    insts = [instance((24, 20), 3), instance((8, 7, 6), 4)]
+    w, U, V, bl, st = run_gpu(insts, 3, precision="fp32_bulk")
+    off = w.cell_offsets()
+    for i, (g, V0, b0, k, s) in enumerate(insts):
+        Ur, Vr, br, nf = run_oracle(g, V0, b0, k, s, 3)
+        assert nf == 0 and st[i] == 0
+        Ui = U[:, off[i]:off[i + 1]]
+        for q in range(12):
+            den = np.abs(Ur[q]).sum()
+            if den > 0:
+                assert np.abs(Ui[q] - Ur[q]).sum() / den < 1e-5, (i, q)
+        assert np.abs(bl[i] - br).sum() / np.abs(br).sum() < 1e-5
+        og = oracle_grid(g)
+        h = min(g["dx"][:g["ndim"]])
+        assert np.abs(O.ct_div(og, bl[i])).max() * h / np.abs(bl[i]).max() < 1e-12
+
+
+def test_ct_option_checks():
     g = rrmhd.make_grid(2, (4, 4), (0.25, 0.25))
-    with pytest.raises(rrmhd.RRMHDError) as e:
-        rrmhd.Context([g], ct=1, precision="fp32_bulk")
-    assert e.value.code == 10
     ctx = rrmhd.Context([g])
     with pytest.raises(rrmhd.RRMHDError) as e:
         ctx.set_face_field(torch.zeros(ctx.num_face_field(), dtype=torch.float64, device="cuda"))
+    assert e.value.code == 10
+    with pytest.raises(rrmhd.RRMHDError) as e:
+        rrmhd.Server(ct=1)
     assert e.value.code == 10
