@@ -301,7 +301,7 @@ class Context:
 
     def autotune(self, repeats=1):
         """Times launch shapes on real steps from the current state (restored after);
-        keeps and returns the fastest (dict) and its median step time in ms."""
+        keeps and returns the fastest (dict) and its best step time in ms."""
         t = rrmhd_tuning()
         ms = C.c_double()
         _check(self.ctx, lib().rrmhd_autotune(self.ctx, int(repeats), C.byref(t), C.byref(ms)))
