@@ -45,9 +45,9 @@ FP64_INST_PER_ZONE = {"fp64": {"faces": 5640.0, "cells": 5439.0},
                       "fp32_bulk": {"faces": None, "cells": 4536.0},
                       "fp64_tangent": {"faces": 5249.0, "cells": 5278.0}}
 # DRAM bytes per cell of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
-TRAFFIC_PER_CELL = {"fp64": {"faces": 248.0, "cells": 1059.0},
-                    "fp32_bulk": {"faces": 166.0, "cells": 962.0},
-                    "fp64_tangent": {"faces": 237.0, "cells": 1061.0}}
+TRAFFIC_PER_CELL = {"fp64": {"faces": 244.0, "cells": 1009.0},
+                    "fp32_bulk": {"faces": 171.0, "cells": 936.0},
+                    "fp64_tangent": {"faces": 235.0, "cells": 1013.0}}
 # Nominal FP64 rate of GB300: 1.25 TFLOP/s = 6.25e11 FP64-pipe instructions/s
 # (2 per SM per clock on 152 SMs at 2.07 GHz); no MEASURED_PEAKS entry exists for FP64.
 FP64_PEAK_INST = 6.25e11
