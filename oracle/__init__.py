@@ -41,7 +41,8 @@ class _Params(C.Structure):
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "c2p_calls", "c2p_iters", "c2p_fail", "flux_evals", "pvm_faces", "pvm_fallback",
-        "imp_cells", "imp_iters", "imp_resid", "imp_jac", "imp_fail", "fallback_cells")]
+        "imp_cells", "imp_iters", "imp_resid", "imp_jac", "imp_fail", "imp_matter", "imp_resid_max",
+        "fallback_cells", "fallback_flagged")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -68,7 +69,7 @@ class Params:
 
     def struct(self):
         p = _Params(self.gamma, self.a_rad, self.cfl, self.pvm_eps, RECON[self.recon],
-                    1 if self.beta else 0, 0 if self.implicit == "newton" else 1, self.pvm_k,
+                    1 if self.beta else 0, {"newton": 0, "picard": 1, "matter": 2}[self.implicit], self.pvm_k,
                     {"pvm": 0, "radhll": 1}[self.solver],
                     self.c2p_maxit, self.imp_maxit, self.imp_tol, 0.0, 0.0)
         lib().or_params_init(C.byref(p))

@@ -169,7 +169,12 @@ static int cell_update(const stage_ctx* s, int i, int j, int k, double Un[12], d
     return rc;
 }
 
-static int inadmissible(int rc) { return rc == OR_EC2P || rc == OR_EUNPHYS; }
+/* A cell update the admissibility fallback retries with first-order faces: no
+ * admissible explicit state, or no converged implicit solve from it. */
+static int retry(int rc) { return rc == OR_EC2P || rc == OR_EUNPHYS || rc == OR_EIMPLICIT; }
+
+/* Passes of the admissibility fallback. */
+#define OR_FALLBACK_PASSES 3
 
 /* One IMEX-RK3 stage (Sec. 3.1):
  *   stage 1: U* = U^(0) + dt L(U^(0)),                         U^(1) = U* + dt S
@@ -177,11 +182,14 @@ static int inadmissible(int rc) { return rc == OR_EC2P || rc == OR_EUNPHYS; }
  *   stage 3: U* = 1/3 U^(0) + 2/3 (U^(2) + dt L(U^(2))),       U^(3) = U* + 2dt/3 S
  * with dt L = -sum_d dt/dx_d (F_{+} - F_{-}) and the source solved implicitly
  * at the new stage state.
- * Admissibility fallback (a posteriori, conservative): cells whose U* has no
- * con2prim root are flagged; every face adjacent to a flagged cell gets the
- * first-order lambda_max = 1 Rusanov flux of the cell-centre states
- * (or_llf_flux), and all cells touching such a face are updated again.  A cell
- * that still fails counts as failed.  Uout/Vout must not alias the inputs. */
+ * Admissibility fallback (a posteriori, conservative), in passes: cells whose U*
+ * has no con2prim root, or whose implicit solve does not converge, are flagged;
+ * in pass p every face adjacent to a cell flagged in pass p gets the first-order
+ * lambda_max = 1 Rusanov flux of the cell-centre states (or_llf_flux), and every
+ * cell touching such a face is updated again.  A re-updated cell that still fails
+ * and was never flagged is flagged for pass p + 1; a failure in the last pass,
+ * or of a cell already flagged, counts as failed.  Uout/Vout must not alias the
+ * inputs. */
 int or_grid_stage_c(const or_params* P, const or_grid* g, int stage, double dt,
                     const double* U0, const double* Us, const double* Vs,
                     const double* kappa, const double* sigma,
@@ -231,6 +239,7 @@ int or_grid_stage_ct(const or_params* P, const or_grid* g, int stage, double dt,
     s.hdt = w * dt;
     for (int d = 0; d < 3; d++) s.dtdx[d] = dt / g->dx[d];
 
+    /* bad[c] = p: the cell was flagged in pass p of the fallback (0: not flagged) */
     unsigned char* bad = (unsigned char*)calloc((size_t)N, 1);
     int nfail = 0, nbad = 0;
     for (int k = 0; k < g->n[2]; k++)
@@ -240,7 +249,7 @@ int or_grid_stage_ct(const or_params* P, const or_grid* g, int stage, double dt,
                 double Un[12], Vn[12];
                 int rc = cell_update(&s, i, j, k, Un, Vn, st);
                 if (cell_status) cell_status[c] = rc;
-                if (inadmissible(rc)) {
+                if (retry(rc)) {
                     bad[c] = 1;
                     nbad++;
                 } else if (rc != OR_OK) {
@@ -252,8 +261,9 @@ int or_grid_stage_ct(const or_params* P, const or_grid* g, int stage, double dt,
                 }
             }
 
-    if (nbad) {
-        /* Rusanov fluxes at every face next to a flagged cell */
+    for (int pass = 1; nbad && pass <= OR_FALLBACK_PASSES; pass++) {
+        nbad = 0;
+        /* Rusanov fluxes at every face next to a cell flagged in this pass */
         for (int d = 0; d < g->ndim; d++) {
             int64_t NF = (int64_t)s.m[d][0] * s.m[d][1] * s.m[d][2];
             for (int k = 0; k < s.m[d][2]; k++)
@@ -263,7 +273,7 @@ int or_grid_stage_ct(const or_params* P, const or_grid* g, int stage, double dt,
                         ql[d] = map_idx(pos[d] - 1, g->n[d], g->bc[d]);
                         qr[d] = map_idx(pos[d], g->n[d], g->bc[d]);
                         int64_t cl = lin(g, ql[0], ql[1], ql[2]), cr = lin(g, qr[0], qr[1], qr[2]);
-                        if (!bad[cl] && !bad[cr]) continue;
+                        if (bad[cl] != pass && bad[cr] != pass) continue;
                         double vl[12], vr[12], F[12];
                         load(Vs, N, cl, vl);
                         load(Vs, N, cr, vr);
@@ -273,12 +283,14 @@ int or_grid_stage_ct(const or_params* P, const or_grid* g, int stage, double dt,
                             if (!ct || q < 5 || q > 7) s.Fh[d][q * NF + fi] = F[q];
                     }
         }
-        /* update again every cell with a changed face: flagged or next to one */
+        /* update again every cell with a changed face: flagged in this pass or
+         * next to such a cell.  A cell that still fails, and was never flagged,
+         * is flagged for the next pass; in the last pass it fails. */
         for (int k = 0; k < g->n[2]; k++)
             for (int j = 0; j < g->n[1]; j++)
                 for (int i = 0; i < g->n[0]; i++) {
                     int64_t c = lin(g, i, j, k);
-                    int hit = bad[c];
+                    int hit = bad[c] == pass;
                     for (int d = 0; d < g->ndim && !hit; d++)
                         for (int e = -1; e <= 1; e += 2) {
                             int q[3] = {i, j, k};
@@ -288,14 +300,20 @@ int or_grid_stage_ct(const or_params* P, const or_grid* g, int stage, double dt,
                             if (pd < 0 || pd >= g->n[d]) {
                                 if (g->bc[d] != OR_BC_PERIODIC) continue;
                             }
-                            if (bad[lin(g, q[0], q[1], q[2])]) hit = 1;
+                            if (bad[lin(g, q[0], q[1], q[2])] == pass) hit = 1;
                         }
                     if (!hit) continue;
                     if (st) st->fallback_cells++;
                     double Un[12], Vn[12];
                     int rc = cell_update(&s, i, j, k, Un, Vn, st);
                     if (cell_status) cell_status[c] = rc;
-                    if (rc != OR_OK) nfail++;
+                    if (retry(rc) && !bad[c] && pass < OR_FALLBACK_PASSES) {
+                        bad[c] = (unsigned char)(pass + 1);
+                        nbad++;
+                        if (st) st->fallback_flagged++;
+                    } else if (rc != OR_OK) {
+                        nfail++;
+                    }
                     for (int q = 0; q < 12; q++) {
                         Uout[q * N + c] = Un[q];
                         Vout[q * N + c] = Vn[q];

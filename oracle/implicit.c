@@ -16,6 +16,12 @@
  * option.  The Picard form diverges once the radiation heat capacity term
  * 4 a_R T^3 h kappa (gamma-1)/rho exceeds about one, which the stiff
  * workloads reach, hence Newton by default.
+ *
+ * Where the radiation carries nearly all the energy, the matter is a small
+ * difference of X and the totals, and the iteration on X loses it.  The same
+ * equations are then solved for the matter primitives Y = (p, u^i) instead,
+ * with X(Y) the totals minus the matter (the MHD-field iteration of Melon
+ * Fuksman & Mignone 2019, the paper's reference for the IMEX M1 scheme).
  */
 #include <math.h>
 #include "oracle.h"
@@ -63,6 +69,37 @@ static int imp_residual(imp_ctx* c, const double X[4], double Zg, double R[4],
     double Pr[3][3], G[4];
     or_m1_pressure(X[0], X + 1, Pr);
     or_four_force(c->kappa, c->sigma, V[0], u, W, BP, X[0], X + 1, Pr, G);
+    for (int i = 0; i < 4; i++) R[i] = (X[i] - c->Xs[i]) + c->hdt * G[i];
+    return 0;
+}
+
+/* The residual as a function of the matter primitives Y = (p, u^i): rho = D/W,
+ * W = sqrt(1 + u.u), v = u/W, B fixed; X = (tau_t - tau_e(Y), S_t - S(Y)).
+ * Returns X and the primitives (matter from Y, radiation X) as well. */
+static int imp_residual_m(imp_ctx* c, const double Y[4], double R[4], double X[4], double V[12])
+{
+    if (c->st) c->st->imp_resid++;
+    if (!(Y[0] > 0.0)) return 1;
+    double W = sqrt(1.0 + ((Y[1] * Y[1] + Y[2] * Y[2]) + Y[3] * Y[3]));
+    double Um[12];
+    V[0] = c->D / W;
+    for (int i = 0; i < 3; i++) {
+        V[1 + i] = Y[1 + i] / W;
+        V[5 + i] = c->B[i];
+        V[9 + i] = 0.0;
+    }
+    V[4] = Y[0];
+    V[8] = 0.0;
+    or_prim2con(c->P, V, Um);
+    X[0] = c->taut - Um[4];
+    for (int i = 0; i < 3; i++) X[1 + i] = c->St[i] - Um[1 + i];
+    if (!(X[0] > 0.0)) return 1;
+    for (int i = 0; i < 4; i++) V[8 + i] = X[i];
+    double T = Y[0] / V[0];
+    double BP = c->P->a_rad * ((T * T) * (T * T));
+    double Pr[3][3], G[4];
+    or_m1_pressure(X[0], X + 1, Pr);
+    or_four_force(c->kappa, c->sigma, V[0], Y + 1, W, BP, X[0], X + 1, Pr, G);
     for (int i = 0; i < 4; i++) R[i] = (X[i] - c->Xs[i]) + c->hdt * G[i];
     return 0;
 }
@@ -305,14 +342,96 @@ static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z,
     return 1;
 }
 
+/* Newton's method on R(Y) = 0 in the matter primitives, from Y: a forward-difference
+ * Jacobian at every iterate (steps 1e-7 of the scales p and 1 + |u|), backtracking on
+ * |R|^2 as in the iteration on X; converged when every component of the full step is
+ * <= 100 imp_tol times its scale.  (R keeps the rounding of the radiation-sized terms,
+ * which the Jacobian, condition ~1e3 where this form is used, carries into Y; the
+ * bound is still far below the matter accuracy of the iteration on X there.)  On
+ * success Y, X and V hold the solution. */
+static int newton_m(imp_ctx* c, double Y[4], double X[4], double V[12])
+{
+    const or_params* P = c->P;
+    double R[4];
+    if (imp_residual_m(c, Y, R, X, V)) return 1;
+    for (int m = 1; m <= P->imp_maxit; m++) {
+        double su = 1.0 + sqrt((Y[1] * Y[1] + Y[2] * Y[2]) + Y[3] * Y[3]);
+        double sc[4] = {Y[0], su, su, su};
+        double J[4][4];
+        for (int j = 0; j < 4; j++) {
+            double Yp[4] = {Y[0], Y[1], Y[2], Y[3]};
+            double Rp[4], Xp[4], Vp[12];
+            Yp[j] = Y[j] + 1e-7 * sc[j];
+            if (imp_residual_m(c, Yp, Rp, Xp, Vp)) {
+                Yp[j] = Y[j] - 1e-7 * sc[j];
+                if (imp_residual_m(c, Yp, Rp, Xp, Vp)) return 1;
+            }
+            double dYj = Yp[j] - Y[j];
+            for (int i = 0; i < 4; i++) J[i][j] = (Rp[i] - R[i]) / dYj;
+        }
+        if (c->st) c->st->imp_jac++;
+        double b[4], dY[4];
+        for (int i = 0; i < 4; i++) b[i] = -R[i];
+        if (or_solve4(J, b, dY)) return 1;
+        if (c->st) c->st->imp_iters++;
+        int conv = 1;
+        for (int i = 0; i < 4; i++)
+            if (fabs(dY[i]) > (100.0 * P->imp_tol) * sc[i]) conv = 0;
+        double Yn[4], Rn[4], Xn[4], Vn[12];
+        if (conv) {
+            for (int i = 0; i < 4; i++) Yn[i] = Y[i] + dY[i];
+            if (imp_residual_m(c, Yn, Rn, Xn, Vn)) return 1;
+            for (int i = 0; i < 4; i++) {
+                Y[i] = Yn[i];
+                X[i] = Xn[i];
+            }
+            for (int k = 0; k < 12; k++) V[k] = Vn[k];
+            return 0;
+        }
+        double r0 = ((R[0] * R[0] + R[1] * R[1]) + R[2] * R[2]) + R[3] * R[3];
+        double lam = 1.0;
+        int ok = 0;
+        for (int k = 0; k < 40; k++) {
+            for (int i = 0; i < 4; i++) Yn[i] = Y[i] + dY[i];
+            if (!imp_residual_m(c, Yn, Rn, Xn, Vn)) {
+                double r1 = ((Rn[0] * Rn[0] + Rn[1] * Rn[1]) + Rn[2] * Rn[2]) + Rn[3] * Rn[3];
+                if (r1 <= (1.0 - 1e-4 * lam) * r0) { ok = 1; break; }
+            }
+            for (int i = 0; i < 4; i++) dY[i] = 0.5 * dY[i];
+            lam = 0.5 * lam;
+        }
+        if (!ok) return 1;
+        for (int i = 0; i < 4; i++) {
+            Y[i] = Yn[i];
+            R[i] = Rn[i];
+            X[i] = Xn[i];
+        }
+        for (int k = 0; k < 12; k++) V[k] = Vn[k];
+    }
+    return 1;
+}
+
+/* The matter-primitive solve from the matter state of U* (primitives Vs). */
+static int solve_matter(imp_ctx* c, const double Vs[12], double X[4], double V[12])
+{
+    if (c->st) c->st->imp_matter++;
+    double v2 = (Vs[1] * Vs[1] + Vs[2] * Vs[2]) + Vs[3] * Vs[3];
+    double W = 1.0 / sqrt(1.0 - v2);
+    double Y[4] = {Vs[4], W * Vs[1], W * Vs[2], W * Vs[3]};
+    return newton_m(c, Y, X, V);
+}
+
 /* jc (may be NULL): the cell's Jacobian cache, 16 entries of M = (J - I)/h from its
  * last converged solve and a validity flag jc[16].  A valid entry is the first
  * matrix of the quasi-Newton iteration instead of C^(m); the converged matrix is
  * stored back (the flag is cleared when the solve fails).  M does not depend on h,
- * so it carries over between stages of different weight. */
-int or_implicit_c(const or_params* P, double kappa, double sigma, double hdt,
-                  const double Ustar[12], double Zguess, double U[12], double V[12], double* jc,
-                  or_stats* st)
+ * so it carries over between stages of different weight.  Flag 2 records that the
+ * last solve needed the matter primitives; the next one starts there.
+ * Order: [flag 2: matter solve]; iteration on X (cache or C^(m)); continuation in
+ * h on X; matter solve (unless it was the first attempt). */
+static int implicit_cell(const or_params* P, double kappa, double sigma, double hdt,
+                         const double Ustar[12], double Zguess, double U[12], double V[12],
+                         double* jc, or_stats* st)
 {
     if (st) st->imp_cells++;
     if ((kappa == 0.0 && sigma == 0.0) || hdt == 0.0) {
@@ -345,9 +464,26 @@ int or_implicit_c(const or_params* P, double kappa, double sigma, double hdt,
     }
     if (P->imp_mode == OR_IMP_PICARD) {
         fail = picard(&c, X, V, &Z);
+    } else if (P->imp_mode == OR_IMP_MATTER) {
+        double Vs[12];
+        for (int k = 0; k < 12; k++) Vs[k] = V[k];
+        fail = solve_matter(&c, Vs, X, V);
     } else {
-        double Mnew[16];
-        fail = newton(&c, X, R, V, &Z, (jc && jc[16] != 0.0) ? jc : 0, Mnew);
+        double Mnew[16], Vs[12];
+        for (int k = 0; k < 12; k++) Vs[k] = V[k];
+        if (jc && jc[16] == 2.0) {
+            /* the cell's last solve needed the matter primitives: start there */
+            if (!solve_matter(&c, Vs, X, V)) {
+                matter_state(&c, X, U);
+                return OR_OK;
+            }
+            for (int i = 0; i < 4; i++) X[i] = c.Xs[i];
+            for (int k = 0; k < 12; k++) V[k] = Vs[k];
+            Z = Zguess;
+            imp_residual(&c, X, Z, R, V, &Z);
+        }
+        int tried_m = jc && jc[16] == 2.0;
+        fail = newton(&c, X, R, V, &Z, (jc && jc[16] == 1.0) ? jc : 0, Mnew);
         if (fail) {
             /* continuation in the implicit weight: solve with h/64, h/32, ..., h,
              * each from the previous solution (the solution moves continuously
@@ -362,9 +498,14 @@ int or_implicit_c(const or_params* P, double kappa, double sigma, double hdt,
             }
             c.hdt = hdt;
         }
+        int matter = 0;
+        if (fail && !tried_m) {
+            fail = solve_matter(&c, Vs, X, V);
+            matter = !fail;
+        }
         if (jc) {
-            for (int k = 0; k < 16; k++) jc[k] = fail ? 0.0 : Mnew[k];
-            jc[16] = fail ? 0.0 : 1.0;
+            for (int k = 0; k < 16; k++) jc[k] = (fail || matter) ? 0.0 : Mnew[k];
+            jc[16] = fail ? 0.0 : (matter ? 2.0 : 1.0);
         }
     }
     if (fail) {
@@ -373,6 +514,16 @@ int or_implicit_c(const or_params* P, double kappa, double sigma, double hdt,
     }
     matter_state(&c, X, U);
     return OR_OK;
+}
+
+int or_implicit_c(const or_params* P, double kappa, double sigma, double hdt,
+                  const double Ustar[12], double Zguess, double U[12], double V[12], double* jc,
+                  or_stats* st)
+{
+    int64_t r0 = st ? st->imp_resid : 0;
+    int rc = implicit_cell(P, kappa, sigma, hdt, Ustar, Zguess, U, V, jc, st);
+    if (st && st->imp_resid - r0 > st->imp_resid_max) st->imp_resid_max = st->imp_resid - r0;
+    return rc;
 }
 
 int or_implicit(const or_params* P, double kappa, double sigma, double hdt,

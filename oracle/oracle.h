@@ -31,7 +31,7 @@ extern "C" {
 
 enum { OR_RECON_GODUNOV = 0, OR_RECON_MINMOD = 1, OR_RECON_MC = 2, OR_RECON_VANLEER = 3 };
 enum { OR_BC_OUTFLOW = 0, OR_BC_PERIODIC = 1 };
-enum { OR_IMP_NEWTON = 0, OR_IMP_PICARD = 1 };
+enum { OR_IMP_NEWTON = 0, OR_IMP_PICARD = 1, OR_IMP_MATTER = 2 };
 enum { OR_SOLVER_PVM = 0, OR_SOLVER_RADHLL = 1 };
 
 /* status codes (per call) */
@@ -49,7 +49,8 @@ typedef struct {
     double pvm_eps;    /* epsilon of the nested flux differences (Sec. 3.2.2, 1e-8) */
     int    recon;      /* OR_RECON_*                                               */
     int    beta_mode;  /* 1: beta = min(1/tau_L, 1/tau_R, 1) (Eq. beta); 0: beta=1  */
-    int    imp_mode;   /* OR_IMP_NEWTON (default) or OR_IMP_PICARD (paper's C matrix) */
+    int    imp_mode;   /* OR_IMP_NEWTON (default), OR_IMP_PICARD (paper's C matrix), or
+                          OR_IMP_MATTER (the matter-primitive iteration alone) */
     int    pvm_k;      /* PVM-int-n with n = 2^k (Eq. iterat): 3 (PVM-int-8), 4 (-16) */
     int    solver;     /* OR_SOLVER_PVM (Sec. 3.2.2) or OR_SOLVER_RADHLL (Sec. 3.2.1)  */
     int    c2p_maxit;  /* Newton iterations allowed in con2prim                    */
@@ -65,7 +66,10 @@ typedef struct {
     int64_t c2p_calls, c2p_iters, c2p_fail;
     int64_t flux_evals, pvm_faces, pvm_fallback;
     int64_t imp_cells, imp_iters, imp_resid, imp_jac, imp_fail;
-    int64_t fallback_cells;
+    int64_t imp_matter;        /* solves in the matter primitives */
+    int64_t imp_resid_max;     /* most residual evaluations of one cell's solve */
+    int64_t fallback_cells;    /* cell updates repeated by the admissibility fallback */
+    int64_t fallback_flagged;  /* cells flagged by it after its first pass */
 } or_stats;
 
 void or_params_init(or_params* P);

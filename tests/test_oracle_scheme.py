@@ -339,6 +339,82 @@ def test_admissibility_fallback_keeps_conservation():
     assert (s2 == 0).all()
 
 
+def _stage_by_hand(G, stage, dt, U0, Us, Vs, kappa, sigma, P, passes=3):
+    """One stage of a 1D periodic grid with the admissibility fallback written out
+    cell by cell from its definition: U* from the face fluxes, the implicit solve,
+    then passes in which every face next to a cell flagged in the pass takes the
+    Rusanov flux and the cells touching such a face are updated again; a cell
+    that still fails, never flagged before, is flagged for the next pass.
+    Returns (U, V, status, the highest pass that flagged a cell)."""
+    n, dtdx = G.n[0], dt / G.dx[0]
+    a, b, w = {1: (0.0, 1.0, 1.0), 2: (0.75, 0.25, 0.25), 3: (1 / 3, 2 / 3, 2 / 3)}[stage]
+    F = O.face_flux(G, 0, Us, Vs, kappa, sigma, P).reshape(12, n + 1)
+    U, V, st = np.empty_like(Us), np.empty_like(Vs), np.zeros(n, dtype=np.int32)
+
+    def update(c):
+        acc = (F[:, c + 1] - F[:, c]) * dtdx
+        Ust = Us[:, c] - acc if stage == 1 else a * U0[:, c] + b * (Us[:, c] - acc)
+        U[:, c], V[:, c], st[c] = O.implicit(Ust, kappa[c], sigma[c], w * dt, P,
+                                             Zguess=O.prim_Z(Vs[:, c], P))
+        return st[c] != 0
+
+    flag = np.zeros(n, dtype=int)
+    for c in range(n):
+        if update(c):
+            flag[c] = 1
+    top = 0
+    for p in range(1, passes + 1):
+        if not (flag == p).any():
+            break
+        top = p
+        for f in range(n + 1):
+            cl, cr = (f - 1) % n, f % n
+            if flag[cl] == p or flag[cr] == p:
+                F[:, f] = O.llf_flux(Vs[:, cl], Vs[:, cr], 0, P)
+        for c in range(n):
+            if p in (flag[c], flag[(c - 1) % n], flag[(c + 1) % n]):
+                if update(c) and flag[c] == 0 and p < passes:
+                    flag[c] = p + 1
+    return U, V, st, top
+
+
+def test_fallback_passes_follow_their_definition():
+    """C1 instance 108 on a periodic grid reaches a second fallback pass (a cell
+    next to a flagged one fails with one first-order face and one PVM face).  The
+    oracle's stages equal the cell-by-cell statement of the passes bit for bit,
+    and stay conservative."""
+    from paper_2212_00370_gb300 import workloads as W
+    w = W.riemann_batch(200, seed=W.SEED_BASE + 1).subset([108])
+    g, V, kappa, sigma = w.instance(0)
+    n = g["n"][0]
+    P = O.Params(gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl)
+    V = np.ascontiguousarray(V).copy()
+    U = O.prim2con(V, P)
+    G = O.Grid(1, (n,), (g["dx"][0],), ("periodic",))
+    tops = []
+    for _ in range(3):
+        dt = O.grid_dt(G, V, P)
+        U0, V0 = U.copy(), V.copy()
+        Us, Vs = U0, V0
+        for s in (1, 2, 3):
+            st = O.Stats()
+            Uo, Vo, cs, nf = O.stage(G, s, dt, U0, Us, Vs, kappa, sigma, P, stats=st)
+            Uh, Vh, ch, top = _stage_by_hand(G, s, dt, U0, Us, Vs, kappa, sigma, P)
+            assert nf == 0
+            np.testing.assert_array_equal(cs, ch)
+            np.testing.assert_array_equal(Uo, Uh)
+            np.testing.assert_array_equal(Vo, Vh)
+            assert (top >= 2) == (st.fallback_flagged > 0)
+            tops.append(top)
+            Us, Vs = Uo, Vo
+        # the source exchanges energy-momentum between matter and radiation only
+        tot = lambda X: np.array([X[0].sum(), (X[4] + X[8]).sum(), *(X[1:4] + X[9:12]).sum(1),
+                                  *X[5:8].sum(1)])
+        assert np.abs(tot(Us) - tot(U0)).max() <= 1e-13 * np.abs(U0).sum()
+        U, V = Us, Vs
+    assert max(tops) >= 2
+
+
 def test_llf_fallback_flux_definition():
     P = O.Params(gamma=4 / 3)
     VL = np.array([1.0, 0.3, 0, 0, 1.0, 0.2, 0.1, 0, 1.0, 0.1, 0, 0])
