@@ -205,8 +205,8 @@ rrmhd_status rrmhd_implicit_source(rrmhd_ctx* ctx, double hdt, const double* Ust
  * the CUDA graph and with CUDA events recorded on the context's stream between
  * launch groups; synchronises.  ms (host, 4): total device time of
  * [0] the 3 face-flux launches, [1] the 3 cell-update launches,
- * [2] the 6 admissibility-fallback launches, [3] the 2 per-instance
- * time-step launches. */
+ * [2] the 18 admissibility-fallback launches (3 passes of faces and cells in
+ * each stage), [3] the 2 per-instance time-step launches. */
 rrmhd_status rrmhd_profile_step(rrmhd_ctx* ctx, double* ms);
 
 /* Kernel launches one rrmhd_imex_step step enqueues (for launch accounting). */
@@ -297,7 +297,11 @@ rrmhd_status rrmhd_cfl_dt_noalloc(const rrmhd_grid* grid, const rrmhd_opts* opts
  *    primitives are copied to the caller's buffer.  Waiting requests are admitted in
  *    arrival order while they fit the resident bounds (cells, faces and slots, from
  *    the memory budget).  The resident state is then repacked into one contiguous
- *    batch: one gather kernel, no host round trip.
+ *    batch: gather kernels, no host round trip.
+ *  - With opts.ct, 2D and 3D requests use constrained transport (Sec. 4) as in a
+ *    context: the staggered face field is built from the request's cell-centred B
+ *    at admission and moves with it in every repack.  The output holds the
+ *    cell-centred primitives (B = the face means).
  *  - One host thread per server (the engine) does all device work, on its own
  *    streams, split into `opts.lanes` concurrent sub-batches.
  * Times are seconds of the host's steady clock since rrmhd_server_create. */
@@ -336,8 +340,8 @@ typedef struct {
 /* Creates a server on the current device and starts its engine thread.
  * opts: host, shared by every request (gamma, precision, lanes, ...); cfg: host or
  * NULL for the defaults.  Device memory for the resident bounds is allocated here,
- * once: about 1.1 KB per resident cell.  Returns EINVAL for bad options, ENOMEM if
- * the allocation fails. */
+ * once: about 1.1 KB per resident cell (1.2 KB with opts.ct).  Returns EINVAL for
+ * bad options, ENOMEM if the allocation fails. */
 rrmhd_status rrmhd_server_create(const rrmhd_opts* opts, const rrmhd_server_config* cfg,
                                  rrmhd_server** out);
 

@@ -58,6 +58,18 @@ struct Batch {
   int64_t e_count[3];
 };
 
+// Passes of the admissibility fallback: a cell that a pass updates again and
+// that still has no admissible update flags its own faces for the next pass.
+constexpr int kFallbackPasses = 3;
+
+// Device counters of one lane: the chunk counters of its persistent launches and,
+// per stage, how many cells each fallback pass flagged (a pass with none returns
+// at once).  Zeroed on the lane's stream by the step that uses them.
+struct LaneCounters {
+  unsigned long long work[2];
+  unsigned int flagged[3][kFallbackPasses + 1];
+};
+
 struct StageArgs {
   Params P;
   Batch b;
@@ -76,7 +88,9 @@ struct StageArgs {
   double* Uout;            // must not alias U0, Us, Vs (the fallback pass re-reads them)
   double* Vout;
   int32_t* cell_status;    // optional per-cell status
-  uint8_t* bad;            // [ncells] cells whose U* is inadmissible (admissibility fallback)
+  uint8_t* bad;            // [ncells] fallback flags: p > 0 = flagged in pass p, 0 = not flagged
+  int fb_pass;             // the admissibility-fallback pass a fallback launch runs, 1..kFallbackPasses
+  unsigned int* flagged;   // [kFallbackPasses + 1]: cells flagged with value p in this stage, or null
   double* jc;              // [17][ncells] per-cell Jacobian cache of the implicit solve
   unsigned long long* work;  // [2] chunk counters of persistent face / cell launches
   // constrained transport (2D/3D instances when ct != 0): the staggered normal
@@ -105,6 +119,7 @@ struct Tuning {
 // shape needs a.work zeroed on the stream before the launch (the launchers do it).
 void launch_faces_f64(const StageArgs& a, const LaunchShape& sh, cudaStream_t s);
 void launch_cells_f64(const StageArgs& a, const LaunchShape& sh, cudaStream_t s);
+// one pass of the admissibility fallback (a.fb_pass): its faces, then its cells
 void launch_fallback_f64(const StageArgs& a, cudaStream_t s);
 void launch_signal_f64(const Params& P, const Batch& b, const double* V, cudaStream_t s);
 // constrained transport: edge EMFs (CT-contact) and the face-field stage update

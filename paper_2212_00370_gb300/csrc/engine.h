@@ -225,7 +225,7 @@ inline Batch make_batch(const Layout& L, const DeviceBufs& B, int i0, int i1) {
 inline StageArgs stage_args(const Params& P, const DeviceBufs& B, const Batch& b, int stage,
                             const double* U0, const double* V0, const double* Us,
                             const double* Vs, double* Uout, double* Vout,
-                            unsigned long long* work = nullptr) {
+                            LaneCounters* cnt = nullptr) {
   StageArgs a;
   a.P = P;
   a.b = b;
@@ -245,8 +245,10 @@ inline StageArgs stage_args(const Params& P, const DeviceBufs& B, const Batch& b
   a.Vout = Vout;
   a.cell_status = nullptr;
   a.bad = B.bad;
+  a.fb_pass = 1;
+  a.flagged = (cnt && stage >= 1) ? cnt->flagged[stage - 1] : nullptr;
   a.jc = B.jc;
-  a.work = work;
+  a.work = cnt ? cnt->work : nullptr;
   a.ct = 0;
   a.fp32_fluxes = 0;
   a.b0 = a.bs = nullptr;
@@ -269,12 +271,20 @@ inline void launch_cells(int precision, const StageArgs& a, const LaunchShape& s
     launch_cells_f64(a, sh, s);
 }
 
+// Every pass of the admissibility fallback; a pass with no flagged cell costs
+// two short launches that return at once.
 inline void launch_fallback(int precision, const StageArgs& a, cudaStream_t s) {
-  if (precision == RRMHD_FP32_BULK)
-    launch_fallback_f32(a, s);
-  else
-    launch_fallback_f64(a, s);
+  StageArgs f = a;
+  for (f.fb_pass = 1; f.fb_pass <= kFallbackPasses; ++f.fb_pass) {
+    if (precision == RRMHD_FP32_BULK)
+      launch_fallback_f32(f, s);
+    else
+      launch_fallback_f64(f, s);
+  }
 }
+
+// Kernel launches of one step on one lane.
+inline int launches_per_step(int ct) { return 2 + 3 * (2 + 2 * kFallbackPasses + (ct ? 2 : 0)); }
 
 // The launch groups of one stage in the given precision and shapes: faces, then
 // (constrained transport) edge EMFs and the face-field update, cells, fallback.
@@ -299,11 +309,12 @@ inline bool tuning_ok(const Tuning& t) {
 // A = S[cur] into B = S[1-cur], with C = (Ub,Vb) for stage 2:
 // stage 1 A -> B, stage 2 (B; A) -> C, stage 3 (C; A) -> B.  No stage writes its
 // inputs, so the admissibility fallback can re-read them.  Launches: begin,
-// 3 x {faces, cells, fallback faces, fallback cells}, end.
-// work: this stream's two chunk counters (persistent shapes).
+// 3 x {faces, [emf, bface,] cells, kFallbackPasses x {fallback faces, fallback
+// cells}}, end (launches_per_step).  The flag counters are zeroed by a memset.
+// cnt: this stream's counters (persistent shapes, fallback passes).
 // ct: constrained transport on (the face-field sets rotate with the state).
 inline void enqueue_step(const Params& P, int precision, const Tuning& tu, const DeviceBufs& B,
-                         const Batch& b, int cur, unsigned long long* work, cudaStream_t s,
+                         const Batch& b, int cur, LaneCounters* cnt, cudaStream_t s,
                          int ct = 0) {
   double* AU = cur ? B.Ua : B.U0;
   double* AV = cur ? B.Va : B.V0;
@@ -312,9 +323,10 @@ inline void enqueue_step(const Params& P, int precision, const Tuning& tu, const
   double* Ab = cur ? B.bfa : B.bf0;
   double* Bb = cur ? B.bf0 : B.bfa;
   launch_begin_step(P, b, s);
-  StageArgs s1 = stage_args(P, B, b, 1, AU, AV, AU, AV, BU, BV, work);
-  StageArgs s2 = stage_args(P, B, b, 2, AU, AV, BU, BV, B.Ub, B.Vb, work);
-  StageArgs s3 = stage_args(P, B, b, 3, AU, AV, B.Ub, B.Vb, BU, BV, work);
+  cudaMemsetAsync(cnt->flagged, 0, sizeof(cnt->flagged), s);
+  StageArgs s1 = stage_args(P, B, b, 1, AU, AV, AU, AV, BU, BV, cnt);
+  StageArgs s2 = stage_args(P, B, b, 2, AU, AV, BU, BV, B.Ub, B.Vb, cnt);
+  StageArgs s3 = stage_args(P, B, b, 3, AU, AV, B.Ub, B.Vb, BU, BV, cnt);
   if (ct) {
     s1.ct = s2.ct = s3.ct = 1;
     s1.fp32_fluxes = s2.fp32_fluxes = s3.fp32_fluxes = (precision == RRMHD_FP32_BULK);
@@ -330,10 +342,6 @@ inline void enqueue_step(const Params& P, int precision, const Tuning& tu, const
   launch_end_step(b, s);
 }
 
-// Kernel launches (and counter memsets, which are graph nodes too) of one step.
-inline int launches_per_step(const Tuning& tu) {
-  return 2 + 3 * (4 + (tu.faces.persistent ? 1 : 0) + (tu.cells.persistent ? 1 : 0));
-}
 
 
 }  // namespace rr

@@ -25,6 +25,12 @@ enum Status : int {
   ST_UNPHYS = 3,    // inadmissible conserved state (D <= 0 or E_r <= 0)
 };
 
+// A cell update the admissibility fallback retries with first-order faces: no
+// admissible explicit state, or no converged implicit solve from it.
+__host__ __device__ inline bool fallback_retry(int rc) {
+  return rc == ST_C2P || rc == ST_IMPLICIT || rc == ST_UNPHYS;
+}
+
 enum Recon : int { RECON_GODUNOV = 0, RECON_MINMOD = 1, RECON_MC = 2, RECON_VANLEER = 3 };
 
 // Scheme constants shared by every kernel of a context (passed by value).

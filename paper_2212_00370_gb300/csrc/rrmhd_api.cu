@@ -22,7 +22,7 @@ using rr::StageArgs;
 
 struct Lane {
   Batch b;                      // the lane's instance / cell / face ranges
-  unsigned long long* work = nullptr;  // the lane's chunk counters (persistent shapes)
+  rr::LaneCounters* cnt = nullptr;  // the lane's counters (persistent shapes, fallback passes)
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per value of rrmhd_ctx::cur
@@ -48,7 +48,7 @@ struct rrmhd_ctx {
   rr::DeviceBufs B;                   // device state and tables
   int cur = 0;                        // the state lives in (U0,V0) when 0, in (Ua,Va) when 1
   rr::Tuning tune;                    // launch shapes
-  unsigned long long* work = nullptr; // chunk counters: 2 per lane, then 2 for whole-batch calls
+  rr::LaneCounters* work = nullptr;   // counters: one set per lane, then one for whole-batch calls
   std::vector<Lane> lanes;
   cudaEvent_t fork = nullptr;
   int* d_flag = nullptr;  // one device int (host-buffer entry)
@@ -112,13 +112,13 @@ void destroy_lanes(rrmhd_ctx* c) {
 rrmhd_status build_lanes(rrmhd_ctx* c, int n) {
   destroy_lanes(c);
   const auto ranges = rr::lane_ranges(c->L.cell_off, c->L.n_inst, n);
-  const size_t nw = 2 * (ranges.size() + 1);
-  RR_CUDA(c, cudaMalloc((void**)&c->work, sizeof(unsigned long long) * nw));
-  RR_CUDA(c, cudaMemset(c->work, 0, sizeof(unsigned long long) * nw));
+  const size_t nw = ranges.size() + 1;
+  RR_CUDA(c, cudaMalloc((void**)&c->work, sizeof(rr::LaneCounters) * nw));
+  RR_CUDA(c, cudaMemset(c->work, 0, sizeof(rr::LaneCounters) * nw));
   for (size_t l = 0; l < ranges.size(); ++l) {
     Lane lane;
     lane.b = rr::make_batch(c->L, c->B, ranges[l].first, ranges[l].second);
-    lane.work = c->work + 2 * l;
+    lane.cnt = c->work + l;
     c->lanes.push_back(lane);
     Lane& L = c->lanes.back();
     RR_CUDA(c, cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking));
@@ -127,8 +127,8 @@ rrmhd_status build_lanes(rrmhd_ctx* c, int n) {
   return RRMHD_OK;
 }
 
-// Chunk counters of the whole-batch launches (flux sweep, profiled step).
-unsigned long long* batch_work(const rrmhd_ctx* c) { return c->work + 2 * c->lanes.size(); }
+// Counters of the whole-batch launches (flux sweep, profiled step).
+rr::LaneCounters* batch_work(const rrmhd_ctx* c) { return c->work + c->lanes.size(); }
 
 }  // namespace
 
@@ -399,7 +399,7 @@ static rrmhd_status build_step_graph(rrmhd_ctx* c, Lane& L, int cur) {
   if (!c->cap_stream)
     RR_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   RR_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  rr::enqueue_step(c->P, c->opts.precision, c->tune, c->B, L.b, cur, L.work, c->cap_stream,
+  rr::enqueue_step(c->P, c->opts.precision, c->tune, c->B, L.b, cur, L.cnt, c->cap_stream,
                    c->opts.ct);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
@@ -485,7 +485,7 @@ rrmhd_status rrmhd_flux_sweep(rrmhd_ctx* c, int dir, double* Fhat) {
   for (int d = 0; d < 3; ++d) b.f_count[d] = (d == dir) ? b.f_count[d] : 0;
   StageArgs a = stage_args(c, b, 0, cur_U(c), cur_V(c), cur_U(c), cur_V(c), nullptr, nullptr);
   a.check_active = 0;
-  a.work = batch_work(c);
+  a.work = batch_work(c)->work;
   if (c->opts.ct) {
     a.ct = 1;
     a.fp32_fluxes = c->opts.precision == RRMHD_FP32_BULK;
@@ -516,7 +516,7 @@ rrmhd_status rrmhd_implicit_source(rrmhd_ctx* c, double hdt, const double* Ustar
 }
 
 int rrmhd_launches_per_step(const rrmhd_ctx* c) {
-  return c ? (int)c->lanes.size() * (2 + 3 * 4) : 0;
+  return c ? (int)c->lanes.size() * rr::launches_per_step(c->opts.ct) : 0;
 }
 
 rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
@@ -527,7 +527,7 @@ rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
   double* AV = cur ? c->B.Va : c->B.V0;
   double* BU = cur ? c->B.U0 : c->B.Ua;
   double* BV = cur ? c->B.V0 : c->B.Va;
-  unsigned long long* w = batch_work(c);
+  rr::LaneCounters* w = batch_work(c);
   StageArgs st[3] = {rr::stage_args(c->P, c->B, b, 1, AU, AV, AU, AV, BU, BV, w),
                      rr::stage_args(c->P, c->B, b, 2, AU, AV, BU, BV, c->B.Ub, c->B.Vb, w),
                      rr::stage_args(c->P, c->B, b, 3, AU, AV, c->B.Ub, c->B.Vb, BU, BV, w)};
@@ -552,6 +552,7 @@ rrmhd_status rrmhd_profile_step(rrmhd_ctx* c, double* ms) {
   int k = 0;
   cudaEventRecord(ev[k++], s);
   rr::launch_begin_step(c->P, b, s);
+  RR_CUDA(c, cudaMemsetAsync(w->flagged, 0, sizeof(w->flagged), s));
   cudaEventRecord(ev[k++], s);
   const int pr = c->opts.precision;
   for (int i = 0; i < 3; ++i) {

@@ -154,9 +154,12 @@ static __device__ __noinline__ void cell_item_f32(const StageArgs& a, int64_t c)
   double Un[NV], Vn[NV];
   const int rc = cell_update_f32(a, c, q, Un, Vn);
   if (a.cell_status) a.cell_status[c] = rc;
-  const bool inadmissible = (rc == ST_C2P || rc == ST_UNPHYS);
-  a.bad[c] = inadmissible ? 1 : 0;
-  if (inadmissible) return;
+  const bool retry = fallback_retry(rc);
+  a.bad[c] = retry ? 1 : 0;
+  if (retry) {
+    if (a.flagged) atomicAdd(a.flagged + 1, 1u);
+    return;
+  }
   if (rc != ST_OK) {
     atomicCAS(a.b.st.status + q.i, 0, rc);
     return;
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(BS) k_cells_f32_persistent(StageArgs a) {
 __global__ void __launch_bounds__(kFaceThreads) k_fallback_faces_f32(StageArgs a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const Batch& b = a.b;
-  if (t >= lane_faces(b)) return;
+  if (t >= lane_faces(b) || (a.flagged && a.flagged[a.fb_pass] == 0)) return;
   const int64_t g = lane_face(b, t);
   const FacePos fp = face_pos(b, g);
   if (!inst_active(b, fp.i)) return;
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(kFaceThreads) k_fallback_faces_f32(StageArgs a
   qr[d] = map_idx(fp.pos[d], I.n[d], I.bc[d]);
   const int64_t cl = I.cell_off + ((int64_t)ql[2] * I.n[1] + ql[1]) * I.n[0] + ql[0];
   const int64_t cr = I.cell_off + ((int64_t)qr[2] * I.n[1] + qr[1]) * I.n[0] + qr[0];
-  if (!a.bad[cl] && !a.bad[cr]) return;
+  if (a.bad[cl] != a.fb_pass && a.bad[cr] != a.fb_pass) return;
   float vl[NV], vr[NV], F[NV];
   load12f(a.Vs, b.ncells, cl, vl);
   load12f(a.Vs, b.ncells, cr, vr);
@@ -215,8 +218,12 @@ __global__ void __launch_bounds__(kCellThreads) k_fallback_cells_f32(StageArgs a
   const int64_t c = b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= b.c_end) return;
   const CellPos q = cell_pos(b, c);
+  const int pass = a.fb_pass;
+  const bool last = pass == kFallbackPasses;
+  const bool none = a.flagged && a.flagged[pass] == 0;  // no cell flagged in this pass
+  if (none && !(a.stage == 3 && last)) return;
   if (!inst_active(b, q.i)) {
-    if (a.stage == 3) {
+    if (a.stage == 3 && last) {
       double u[NV], v[NV];
       load12(a.U0, b.ncells, c, u);
       load12(a.V0, b.ncells, c, v);
@@ -225,14 +232,14 @@ __global__ void __launch_bounds__(kCellThreads) k_fallback_cells_f32(StageArgs a
     return;
   }
   const InstDesc& I = q.I;
-  bool hit = a.bad[c] != 0;
-  for (int d = 0; d < I.ndim && !hit; ++d) {
+  bool hit = !none && a.bad[c] == pass;
+  for (int d = 0; d < I.ndim && !hit && !none; ++d) {
     for (int e = -1; e <= 1; e += 2) {
       const int pd = q.p[d] + e;
       if ((pd < 0 || pd >= I.n[d]) && I.bc[d] != 1) continue;
       int r[3] = {q.p[0], q.p[1], q.p[2]};
       r[d] = map_idx(pd, I.n[d], I.bc[d]);
-      if (a.bad[I.cell_off + ((int64_t)r[2] * I.n[1] + r[1]) * I.n[0] + r[0]]) hit = true;
+      if (a.bad[I.cell_off + ((int64_t)r[2] * I.n[1] + r[1]) * I.n[0] + r[0]] == pass) hit = true;
     }
   }
   double Vn[NV];
@@ -240,15 +247,20 @@ __global__ void __launch_bounds__(kCellThreads) k_fallback_cells_f32(StageArgs a
     double Un[NV];
     const int rc = cell_update_f32(a, c, q, Un, Vn);
     if (a.cell_status) a.cell_status[c] = rc;
+    if (fallback_retry(rc) && a.bad[c] == 0 && !last) {
+      a.bad[c] = (uint8_t)(pass + 1);  // its faces go first-order in the next pass
+      if (a.flagged) atomicAdd(a.flagged + pass + 1, 1u);
+      return;
+    }
     if (rc != ST_OK) {
       atomicCAS(b.st.status + q.i, 0, rc);
       return;
     }
     store_cell(a, c, Un, Vn);
-  } else if (a.stage == 3) {
+  } else if (a.stage == 3 && last) {
     load12(a.Vout, b.ncells, c, Vn);
   }
-  if (a.stage == 3) {
+  if (a.stage == 3 && last) {
     double s = signal_speed(a.P, 0, Vn) / I.dx[0];
     for (int d = 1; d < I.ndim; ++d) s = s + signal_speed(a.P, d, Vn) / I.dx[d];
     atomicMax(b.st.smax + q.i, (unsigned long long)__double_as_longlong(s));

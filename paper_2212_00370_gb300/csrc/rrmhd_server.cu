@@ -5,9 +5,11 @@
 // One engine thread owns all device work.  Its loop:
 //   1. admit waiting requests in arrival order while they fit the resident bounds;
 //   2. when the resident set changed: repack it into one contiguous batch
-//      (survivors first, in their old order, then the new requests) by a gather
-//      kernel from the current buffers into the spare ones, upload the new
-//      requests' primitives and compute their conserved state and signal speeds;
+//      (survivors first, in their old order, then the new requests) by gather
+//      kernels from the current buffers into the spare ones (cells, and with
+//      constrained transport the staggered face field), upload the new
+//      requests' primitives and compute their face field (constrained
+//      transport), conserved state and signal speeds;
 //   3. one IMEX step of every resident request (lanes on their own streams);
 //   4. read back t, status and the next CFL maximum of every resident request,
 //      copy out the finished ones and complete them.
@@ -43,7 +45,11 @@ using rr::Params;
 // Bytes the server holds per resident cell: six 12-plane state buffers, two
 // copies of kappa, sigma and the 17-plane Jacobian cache, one fallback flag.
 constexpr int64_t kBytesPerCell = 6 * 12 * 8 + 2 * (1 + 1 + 17) * 8 + 1;
-constexpr int64_t kBytesPerFace = 12 * 8;
+// Per unit of face capacity: the 12-plane flux buffer; with constrained
+// transport also the three staggered face-field sets and two edge EMFs (a
+// request takes max(faces, edges / 2) units, so the edges fit in twice the
+// face capacity).
+inline int64_t bytes_per_face(int ct) { return 12 * 8 + (ct ? (3 + 2) * 8 : 0); }
 // Face capacity per cell capacity: covers 2D grids of any size (2(n+1)/n faces
 // per cell for n >= 40); 3D requests are bounded by the faces they need.
 constexpr double kFacesPerCell = 2.05;
@@ -60,6 +66,17 @@ struct PlaneGroup {
   const double* src;
   double* dst;
   int planes;
+};
+
+struct FaceGatherArgs {
+  int n_inst;                        // survivors
+  int n_all;                         // instances of the new layout
+  const int64_t* new_off;            // [3][n_all + 1] face offsets of the new layout
+  const int64_t* src_off;            // [3][n_inst] survivors' face offsets in the old layout
+  int64_t new_base[3], old_base[3];  // direction bases of the two layouts
+  int64_t cnt[3];                    // survivors' faces per direction
+  const double* src;
+  double* dst;
 };
 
 struct GatherArgs {
@@ -83,6 +100,20 @@ __global__ void __launch_bounds__(kThreads) k_gather(GatherArgs a) {
   }
 }
 
+// Survivors' staggered face field to the new layout, direction by direction.
+__global__ void __launch_bounds__(kThreads) k_gather_faces(FaceGatherArgs a) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int d = 0;
+  while (d < 3 && t >= a.cnt[d]) {
+    t -= a.cnt[d];
+    ++d;
+  }
+  if (d == 3) return;
+  const int64_t* no = a.new_off + (int64_t)d * (a.n_all + 1);
+  const int i = rr::idx::find_inst(no, 0, a.n_inst, t);
+  a.dst[a.new_base[d] + t] = a.src[a.old_base[d] + a.src_off[(int64_t)d * a.n_inst + i] + (t - no[i])];
+}
+
 // New requests' cells [c0, c1): U = prim2con(V) (Eq. eqU) and an empty Jacobian cache.
 __global__ void __launch_bounds__(kThreads) k_admit(Params P, const double* __restrict__ V,
                                                      double* __restrict__ U, double* __restrict__ jc,
@@ -104,13 +135,15 @@ using Clock = std::chrono::steady_clock;
 struct Request {
   int64_t id = 0;
   rrmhd_grid grid{};
-  int64_t cells = 0, faces = 0;
+  int64_t cells = 0;
+  int64_t faces = 0;  // face-capacity units: faces, or max(faces, edges / 2) with constrained transport
   std::vector<double> V, kappa, sigma;  // host copies of the inputs
   double t_end = 0.0;
   double* out = nullptr;                // caller's host buffer
   rrmhd_result res{};
   // resident bookkeeping (engine thread only)
   int64_t off = 0;  // cell offset in the current layout
+  int slot = 0;     // instance index in the current layout
   double t = 0.0;
   unsigned long long smax = 0ull;
   int status = 0;
@@ -136,7 +169,8 @@ struct rrmhd_server {
   rr::DeviceBufs B;
   double *kap[2] = {nullptr, nullptr}, *sig[2] = {nullptr, nullptr}, *jcb[2] = {nullptr, nullptr};
   int64_t* d_src_off = nullptr;
-  unsigned long long* work = nullptr;  // chunk counters, 2 per lane
+  int64_t* d_src_foff = nullptr;       // [3][slots] survivors' old face offsets (constrained transport)
+  rr::LaneCounters* work = nullptr;    // counters, one set per lane
   rr::Tuning tune;                     // launch shapes
   int kc = 0;   // live copy of kappa / sigma / jc
   int cur = 0;  // the state lives in (U0,V0) when 0, in (Ua,Va) when 1
@@ -193,11 +227,22 @@ bool relayout(rrmhd_server* s, int n_surv) {
   for (int i = 0; i < n; ++i) grids[i] = s->res[i]->grid;
   for (int i = 0; i < n_surv; ++i) src_off[i] = s->res[i]->off;
   const int64_t n_old = s->L.ncells;
+  const int ct = s->opts.ct;
+  std::vector<int64_t> src_foff(3 * (size_t)n_surv);
+  int64_t old_base[3];
+  for (int d = 0; d < 3; ++d) {
+    old_base[d] = s->L.dir_base[d];
+    for (int i = 0; i < n_surv; ++i)
+      src_foff[(size_t)d * n_surv + i] = s->L.face_off[(size_t)d * (s->L.n_inst + 1) + s->res[i]->slot];
+  }
   s->L = rr::make_layout(grids.data(), n);
   const rr::Layout& L = s->L;
   rr::DeviceBufs& B = s->B;
   cudaStream_t st = s->stream;
-  for (int i = 0; i < n; ++i) s->res[i]->off = L.cell_off[i];
+  for (int i = 0; i < n; ++i) {
+    s->res[i]->off = L.cell_off[i];
+    s->res[i]->slot = i;
+  }
   if (n == 0) return true;
 
   // tables of the new layout (the previous step has completed: the stream is idle)
@@ -205,6 +250,8 @@ bool relayout(rrmhd_server* s, int n_surv) {
   SRV_CUDA(s, cudaMemcpyAsync(B.cell_off, L.cell_off.data(), sizeof(int64_t) * (n + 1),
                               cudaMemcpyHostToDevice, st));
   SRV_CUDA(s, cudaMemcpyAsync(B.face_off, L.face_off.data(), sizeof(int64_t) * 3 * (n + 1),
+                              cudaMemcpyHostToDevice, st));
+  SRV_CUDA(s, cudaMemcpyAsync(B.edge_off, L.edge_off.data(), sizeof(int64_t) * 3 * (n + 1),
                               cudaMemcpyHostToDevice, st));
   for (int i = 0; i < n; ++i) {
     const Request& r = *s->res[i];
@@ -241,6 +288,26 @@ bool relayout(rrmhd_server* s, int n_surv) {
     a.g[4] = {s->jcb[ko], s->jcb[kn], 17};
     k_gather<<<grid_for(L.cell_off[n_surv], kThreads), kThreads, 0, st>>>(a);
     SRV_CUDA(s, cudaGetLastError());
+    if (ct) {
+      SRV_CUDA(s, cudaMemcpyAsync(s->d_src_foff, src_foff.data(), sizeof(int64_t) * 3 * n_surv,
+                                  cudaMemcpyHostToDevice, st));
+      FaceGatherArgs f;
+      f.n_inst = n_surv;
+      f.n_all = n;
+      f.new_off = B.face_off;
+      f.src_off = s->d_src_foff;
+      int64_t total = 0;
+      for (int d = 0; d < 3; ++d) {
+        f.new_base[d] = L.dir_base[d];
+        f.old_base[d] = old_base[d];
+        f.cnt[d] = L.face_off[(size_t)d * (n + 1) + n_surv];
+        total += f.cnt[d];
+      }
+      f.src = s->cur ? B.bfa : B.bf0;
+      f.dst = s->cur ? B.bf0 : B.bfa;
+      if (total > 0) k_gather_faces<<<grid_for(total, kThreads), kThreads, 0, st>>>(f);
+      SRV_CUDA(s, cudaGetLastError());
+    }
   }
   // new requests: primitives and opacities from the host, then U, cache, speeds
   for (int i = n_surv; i < n; ++i) {
@@ -260,9 +327,17 @@ bool relayout(rrmhd_server* s, int n_surv) {
   B.jc = s->jcb[kn];
   if (n_surv < n) {
     const int64_t c0 = L.cell_off[n_surv], c1 = L.ncells;
+    const Batch nb = rr::make_batch(L, B, n_surv, n);
+    if (ct) {  // as a context's set_state: faces from the cells, duplicates, cells from the faces
+      double* bnew = s->cur ? B.bfa : B.bf0;  // s->cur already names the new buffers
+      rr::launch_faces_from_cells_f64(nb, Vnew, bnew, st);
+      rr::launch_ct_canonical_f64(nb, bnew, st);
+      rr::launch_cells_from_faces_f64(nb, bnew, Vnew, st);
+      SRV_CUDA(s, cudaGetLastError());
+    }
     k_admit<<<grid_for(c1 - c0, kThreads), kThreads, 0, st>>>(s->P, Vnew, Unew, B.jc, L.ncells, c0, c1);
     SRV_CUDA(s, cudaGetLastError());
-    rr::launch_signal_f64(s->P, rr::make_batch(L, B, n_surv, n), Vnew, st);
+    rr::launch_signal_f64(s->P, nb, Vnew, st);
     SRV_CUDA(s, cudaGetLastError());
   }
   SRV_CUDA(s, cudaStreamSynchronize(st));  // the host copies of the inputs may now go
@@ -291,7 +366,7 @@ bool step(rrmhd_server* s, std::vector<rrmhd_result>& finished, int64_t& zone_up
     SRV_CUDA(s, cudaStreamWaitEvent(ln.stream, s->fork, 0));
     rr::enqueue_step(s->P, s->opts.precision, s->tune, s->B,
                      rr::make_batch(L, s->B, ranges[l].first, ranges[l].second), s->cur,
-                     s->work + 2 * l, ln.stream);
+                     s->work + l, ln.stream, s->opts.ct);
     SRV_CUDA(s, cudaGetLastError());
     SRV_CUDA(s, cudaEventRecord(ln.done, ln.stream));
   }
@@ -447,10 +522,11 @@ void free_server(rrmhd_server* s) {
   if (s->fork) cudaEventDestroy(s->fork);
   if (s->stream) cudaStreamDestroy(s->stream);
   rr::DeviceBufs& B = s->B;
-  void* bufs[] = {B.inst,    B.cell_off, B.face_off, B.U0,      B.Ua,      B.Ub,
-                  B.V0,      B.Va,       B.Vb,       B.Fhat,    B.bad,     B.t,
-                  B.t_end,   B.dt,       B.smax,     B.status,  s->kap[0], s->kap[1],
-                  s->sig[0], s->sig[1],  s->jcb[0],  s->jcb[1], s->d_src_off, s->work};
+  void* bufs[] = {B.inst,    B.cell_off, B.face_off, B.edge_off,  B.U0,          B.Ua,
+                  B.Ub,      B.V0,       B.Va,       B.Vb,        B.Fhat,        B.bad,
+                  B.bf0,     B.bfa,      B.bfb,      B.emf,       B.t,           B.t_end,
+                  B.dt,      B.smax,     B.status,   s->kap[0],   s->kap[1],     s->sig[0],
+                  s->sig[1], s->jcb[0],  s->jcb[1],  s->d_src_off, s->d_src_foff, s->work};
   for (void* p : bufs)
     if (p) cudaFree(p);
   void* hbufs[] = {s->h_t, s->h_tend, s->h_smax, s->h_status};
@@ -479,7 +555,7 @@ rrmhd_status rrmhd_server_create(const rrmhd_opts* opts, const rrmhd_server_conf
                                  rrmhd_server** out) {
   if (!out) return RRMHD_EINVAL;
   *out = nullptr;
-  if (!opts || !rr::opts_ok(*opts) || opts->ct) return RRMHD_EINVAL;  // no face field in the server
+  if (!opts || !rr::opts_ok(*opts)) return RRMHD_EINVAL;
   rrmhd_server_config c{};
   if (cfg) c = *cfg;
   if (c.mem_bytes < 0 || c.max_resident_cells < 0 || c.max_resident < 0) return RRMHD_EINVAL;
@@ -513,7 +589,7 @@ rrmhd_status rrmhd_server_create(const rrmhd_opts* opts, const rrmhd_server_conf
     mem = (int64_t)(fr / 2);
   }
   s->cap_slots = c.max_resident > 0 ? c.max_resident : kDefaultSlots;
-  s->cap_cells = (int64_t)(mem / (kBytesPerCell + kFacesPerCell * kBytesPerFace));
+  s->cap_cells = (int64_t)(mem / (kBytesPerCell + kFacesPerCell * bytes_per_face(opts->ct)));
   if (c.max_resident_cells > 0) s->cap_cells = std::min(s->cap_cells, c.max_resident_cells);
   if (s->cap_cells < 1) return fail(RRMHD_EINVAL);
   s->cap_faces = (int64_t)(kFacesPerCell * (double)s->cap_cells) + 64;
@@ -536,13 +612,19 @@ rrmhd_status rrmhd_server_create(const rrmhd_opts* opts, const rrmhd_server_conf
   A((void**)&B.inst, sizeof(InstDesc) * I);
   A((void**)&B.cell_off, sizeof(int64_t) * (I + 1));
   A((void**)&B.face_off, sizeof(int64_t) * 3 * (I + 1));
+  A((void**)&B.edge_off, sizeof(int64_t) * 3 * (I + 1));
+  if (opts->ct) {
+    for (double** p : {&B.bf0, &B.bfa, &B.bfb}) A((void**)p, sizeof(double) * F);
+    A((void**)&B.emf, sizeof(double) * 2 * F);
+    A((void**)&s->d_src_foff, sizeof(int64_t) * 3 * I);
+  }
   A((void**)&B.t, sizeof(double) * I);
   A((void**)&B.t_end, sizeof(double) * I);
   A((void**)&B.dt, sizeof(double) * I);
   A((void**)&B.smax, sizeof(unsigned long long) * I);
   A((void**)&B.status, sizeof(int) * I);
   A((void**)&s->d_src_off, sizeof(int64_t) * I);
-  A((void**)&s->work, sizeof(unsigned long long) * 2 * lanes);
+  A((void**)&s->work, sizeof(rr::LaneCounters) * lanes);
   if (!ok) {
     cudaGetLastError();  // clear the allocation error
     return fail(RRMHD_ENOMEM);
@@ -582,6 +664,11 @@ rrmhd_status rrmhd_server_submit(rrmhd_server* s, const rrmhd_grid* grid, const 
   r->grid = *grid;
   r->cells = rr::grid_cells(*grid);
   r->faces = rr::grid_faces(*grid);
+  if (s->opts.ct) {
+    int64_t edges = 0;
+    for (int e = 0; e < 3; ++e) edges += rr::grid_edges(*grid, e);
+    r->faces = std::max(r->faces, (edges + 1) / 2);
+  }
   if (r->cells > s->max_cells || r->faces > s->cap_faces) return RRMHD_ECAPACITY;
   r->V.assign(V, V + 12 * r->cells);
   r->kappa.assign(kappa, kappa + r->cells);

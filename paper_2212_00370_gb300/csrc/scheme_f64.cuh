@@ -467,10 +467,141 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
 
 constexpr int IMP_LADDER = 6;  // continuation fallback starts at h / 2^6
 
+// The same residual as a function of the matter primitives Y = (p, u^i):
+// rho = D/W, W = sqrt(1 + u.u), v = u/W, B fixed, X = (tau_t - tau_e(Y), S_t - S(Y)).
+// Where the radiation carries nearly all the energy the matter is a small
+// difference of X and the totals, and the iteration on X loses it; this form
+// keeps it (the MHD-field iteration of Melon Fuksman & Mignone 2019).  Also
+// returns X and the primitives (matter from Y, radiation X).
+static __device__ __noinline__ bool imp_residual_m(const Params& P, const ImpCell& c,
+                                                   const double* Y, double* R, double* X,
+                                                   double* V) {
+  if (!(Y[0] > 0.0)) return false;
+  const double W = sqrt(1.0 + ((Y[1] * Y[1] + Y[2] * Y[2]) + Y[3] * Y[3]));
+  double Um[NV];
+  V[0] = c.D / W;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    V[1 + i] = Y[1 + i] / W;
+    V[5 + i] = c.B[i];
+    V[9 + i] = 0.0;
+  }
+  V[4] = Y[0];
+  V[8] = 0.0;
+  prim2con(P, V, Um);
+  X[0] = c.taut - Um[4];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) X[1 + i] = c.St[i] - Um[1 + i];
+  if (!(X[0] > 0.0)) return false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) V[8 + i] = X[i];
+  const double T = Y[0] / V[0];
+  const double BP = P.a_rad * ((T * T) * (T * T));
+  const M1 m = m1_coef(X[0], X[1], X[2], X[3]);
+  double Pr[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Pr[i][j] = m1_P(m, X + 1, i, j);
+  double G[4];
+  four_force(c.kappa, c.sigma, V[0], Y + 1, W, BP, X[0], X + 1, Pr, G);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) R[i] = (X[i] - c.Xs[i]) + c.hdt * G[i];
+  return true;
+}
+
+// Newton's method on R(Y) = 0 from Y: forward-difference Jacobian at every iterate
+// (steps 1e-7 of the scales p and 1 + |u|), backtracking on |R|^2; converged when
+// every component of the full step is <= 100 imp_tol times its scale (R keeps the
+// rounding of the radiation-sized terms, which the Jacobian carries into Y).
+static __device__ __noinline__ bool imp_newton_m(const Params& P, const ImpCell& c, double* Y,
+                                                 double* X, double* V) {
+  double R[4];
+  if (!imp_residual_m(P, c, Y, R, X, V)) return false;
+  for (int m = 1; m <= P.imp_maxit; ++m) {
+    const double su = 1.0 + sqrt((Y[1] * Y[1] + Y[2] * Y[2]) + Y[3] * Y[3]);
+    const double sc[4] = {Y[0], su, su, su};
+    double J[4][4];
+    for (int j = 0; j < 4; ++j) {
+      double Yp[4] = {Y[0], Y[1], Y[2], Y[3]};
+      double Rp[4], Xp[4], Vp[NV];
+      Yp[j] = Y[j] + 1e-7 * sc[j];
+      if (!imp_residual_m(P, c, Yp, Rp, Xp, Vp)) {
+        Yp[j] = Y[j] - 1e-7 * sc[j];
+        if (!imp_residual_m(P, c, Yp, Rp, Xp, Vp)) return false;
+      }
+      const double dYj = Yp[j] - Y[j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) J[i][j] = (Rp[i] - R[i]) / dYj;
+    }
+    double b[4], dY[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = -R[i];
+    if (!solve4(J, b, dY)) return false;
+    bool conv = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (fabs(dY[i]) > (100.0 * P.imp_tol) * sc[i]) conv = false;
+    double Yn[4], Rn[4], Xn[4], Vn[NV];
+    if (conv) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Yn[i] = Y[i] + dY[i];
+      if (!imp_residual_m(P, c, Yn, Rn, Xn, Vn)) return false;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        Y[i] = Yn[i];
+        X[i] = Xn[i];
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) V[k] = Vn[k];
+      return true;
+    }
+    const double r0 = ((R[0] * R[0] + R[1] * R[1]) + R[2] * R[2]) + R[3] * R[3];
+    double lam = 1.0;
+    bool ok = false;
+    for (int k = 0; k < 40; ++k) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Yn[i] = Y[i] + dY[i];
+      if (imp_residual_m(P, c, Yn, Rn, Xn, Vn)) {
+        const double r1 = ((Rn[0] * Rn[0] + Rn[1] * Rn[1]) + Rn[2] * Rn[2]) + Rn[3] * Rn[3];
+        if (r1 <= (1.0 - 1e-4 * lam) * r0) {
+          ok = true;
+          break;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) dY[i] = 0.5 * dY[i];
+      lam = 0.5 * lam;
+    }
+    if (!ok) return false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      Y[i] = Yn[i];
+      R[i] = Rn[i];
+      X[i] = Xn[i];
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) V[k] = Vn[k];
+  }
+  return false;
+}
+
+// The matter-primitive solve from the matter state of U* (primitives Vs).
+__device__ __forceinline__ bool solve_matter(const Params& P, const ImpCell& c, const double* Vs,
+                                             double* X, double* V) {
+  const double v2 = (Vs[1] * Vs[1] + Vs[2] * Vs[2]) + Vs[3] * Vs[3];
+  const double W = 1.0 / sqrt(1.0 - v2);
+  double Y[4] = {Vs[4], W * Vs[1], W * Vs[2], W * Vs[3]};
+  return imp_newton_m(P, c, Y, X, V);
+}
+
 // Implicit step of one cell (Sec. 3.3).  Writes U and V on success; returns a Status.
 // jc (may be null): the cell's Jacobian cache, M = (J - I)/h of its last converged
-// solve (16 entries) and a validity flag jc[16]; a valid entry replaces C^(m) as the
-// first matrix, and the converged matrix is stored back (cleared on failure).
+// solve (16 entries) and a flag jc[16]; with flag 1 M replaces C^(m) as the first
+// matrix, and the converged matrix is stored back (cleared on failure).  Flag 2: the
+// last solve needed the matter primitives, and the next one starts there.  Order:
+// [flag 2: matter solve]; iteration on X; continuation in h on X; matter solve
+// (unless it was the first attempt).
 __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, double sigma,
                                              double hdt, const double* Us, double Zguess,
                                              double* U, double* V, double* jc = nullptr) {
@@ -496,8 +627,23 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
   double R[4], Z = Zguess;
   // no admissible matter state at X*: the explicit update U* itself is inadmissible
   if (!imp_residual(P, c, X, Zguess, R, V, &Z)) return ST_C2P;
-  double Mnew[16];
-  bool ok = imp_newton(P, c, X, R, V, &Z, (jc && jc[16] != 0.0) ? jc : nullptr, Mnew);
+  double Mnew[16], Vs[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) Vs[k] = V[k];
+  const bool tried_m = jc && jc[16] == 2.0;
+  if (tried_m) {
+    if (solve_matter(P, c, Vs, X, V)) {
+      matter_state(c, X, U);
+      return ST_OK;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) X[i] = c.Xs[i];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) V[k] = Vs[k];
+    Z = Zguess;
+    imp_residual(P, c, X, Z, R, V, &Z);
+  }
+  bool ok = imp_newton(P, c, X, R, V, &Z, (jc && jc[16] == 1.0) ? jc : nullptr, Mnew);
   if (!ok) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) X[i] = c.Xs[i];
@@ -508,11 +654,17 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
       ok = imp_residual(P, c, X, Z, R, V, &Z);
       if (ok) ok = imp_newton(P, c, X, R, V, &Z, nullptr, Mnew);
     }
+    c.hdt = hdt;
+  }
+  bool matter = false;
+  if (!ok && !tried_m) {
+    ok = solve_matter(P, c, Vs, X, V);
+    matter = ok;
   }
   if (jc) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) jc[k] = ok ? Mnew[k] : 0.0;
-    jc[16] = ok ? 1.0 : 0.0;
+    for (int k = 0; k < 16; ++k) jc[k] = (ok && !matter) ? Mnew[k] : 0.0;
+    jc[16] = ok ? (matter ? 2.0 : 1.0) : 0.0;
   }
   if (!ok) return ST_IMPLICIT;
   matter_state(c, X, U);

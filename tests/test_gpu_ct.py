@@ -178,6 +178,3 @@ def test_ct_option_checks():
     with pytest.raises(rrmhd.RRMHDError) as e:
         ctx.set_face_field(torch.zeros(ctx.num_face_field(), dtype=torch.float64, device="cuda"))
     assert e.value.code == 10
-    with pytest.raises(rrmhd.RRMHDError) as e:
-        rrmhd.Server(ct=1)
-    assert e.value.code == 10

@@ -1,0 +1,103 @@
+"""The robustness paths of the step on the GPU against the oracle, FP64 bit for bit:
+
+  * the admissibility fallback's passes, on the C1 instances whose first steps
+    need them most: cells whose explicit update has no con2prim root next to
+    cells that then fail with one first-order face (a second pass), and cells
+    whose implicit solve does not converge until their faces go first-order;
+  * the implicit solve in the matter primitives, on radiation-dominated cells
+    where the iteration on X fails (through rrmhd_implicit_source), and over
+    many steps of the 2D blast (128^2, constrained transport), where it, the
+    fallback passes and the per-cell record of the form used all take part.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_helpers import compare_bitwise, gpu_context, oracle_grid, oracle_params, oracle_run_instance
+from paper_2212_00370_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# C1 (4096 instances): second-pass cases, then implicit-solve cases
+HARD = [32, 744, 888, 1744, 2808, 3616, 24, 440, 1160, 1728]
+
+# a radiation-dominated cell of the 2D blast (E_r ~ 1e6 x the gas energy, W ~ 2.6)
+RAD_DOMINATED = np.array([0.285, 0.266, 0.873, 0.0, 9.17, 0.335, 0.0405, 0.0,
+                          8.33e6, 2.30e6, 7.63e6, 0.0])
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2212_00370_gb300 import build
+    build.build()
+
+
+def test_fallback_passes_bitwise_c1_hard_instances():
+    w = W.riemann_batch().subset(HARD)
+    ctx = gpu_context(w)
+    ctx.imex_step(13)
+    U, V = (x.cpu().numpy() for x in ctx.get_state())
+    t, _ = ctx.get_times()
+    st = ctx.inst_status()
+    off = w.cell_offsets()
+    for i in range(w.n_inst):
+        Ur, Vr, tr, steps, nfail = oracle_run_instance(w, i, 13)
+        assert (st[i] != 0) == (nfail != 0), (HARD[i], st[i], nfail)
+        s = slice(off[i], off[i + 1])
+        compare_bitwise(U[:, s], Ur, f"instance {HARD[i]} U")
+        compare_bitwise(V[:, s], Vr, f"instance {HARD[i]} V")
+        assert t[i] == tr
+    # every one of them runs through (one pass, or an implicit failure, used to stop them)
+    assert (st == 0).all(), st
+
+
+@pytest.mark.parametrize("hdt", [1.9e-3, 3e-3, 5e-3])
+def test_matter_form_implicit_source_bitwise(hdt):
+    """Perturbed radiation-dominated cells: where the iteration on X fails the
+    matter-primitive solve takes over, on both sides the same way."""
+    rng = np.random.default_rng(5)
+    n = 256
+    V = RAD_DOMINATED[:, None] * (1 + 0.05 * rng.uniform(-1, 1, (12, n)))
+    V[8] = 10 ** rng.uniform(5, 7, n)
+    V[9:12] = RAD_DOMINATED[9:12, None] / RAD_DOMINATED[8] * V[8] * rng.uniform(0.8, 1.0, n)
+    w = W.Workload("rad-dominated", [W.grid1d(n)], np.ascontiguousarray(V), 10 ** rng.uniform(-0.5, 1, n),
+                   np.zeros(n), np.array([1.0]), 4 / 3)
+    P = oracle_params(w)
+    Us = O.prim2con(V, P)
+    Zg = O.prim_Z(V, P)
+    st_o = O.Stats()
+    U_ref, V_ref, st_ref = O.implicit(Us, w.kappa, w.sigma, hdt, P, Zguess=Zg, stats=st_o)
+    ctx = gpu_context(w)
+    U, Vg, st = ctx.implicit_source(hdt, torch.tensor(Us, device="cuda"), torch.tensor(Zg, device="cuda"))
+    compare_bitwise(st.cpu().numpy(), st_ref, "implicit status")
+    ok = st_ref == 0
+    compare_bitwise(U.cpu().numpy()[:, ok], U_ref[:, ok], "implicit U")
+    compare_bitwise(Vg.cpu().numpy()[:, ok], V_ref[:, ok], "implicit V")
+    assert st_o.imp_matter > 0
+
+
+def test_blast_2d_many_steps_bitwise():
+    """C2's set-up at 128^2 with constrained transport, 30 steps: the oracle needs
+    the matter-primitive solve and the fallback passes on this run."""
+    w = W.blast_2d(128)
+    P = oracle_params(w)
+    g, V0, k, s = w.instance(0)
+    og = oracle_grid(g)
+    V = np.ascontiguousarray(V0).copy()
+    b = O.ct_faces_from_cells(og, V)
+    O.ct_canonical(og, b)
+    O.ct_cells_from_faces(og, b, np.zeros_like(V), V)
+    U = O.prim2con(V, P)
+    st_o = O.Stats()
+    t, steps, nfail = O.run(og, 0.0, np.inf, U, V, k, s, P, max_steps=30, stats=st_o, bface=b)
+    assert nfail == 0 and steps == 30
+    assert st_o.imp_matter > 0 and st_o.fallback_cells > 0
+    ctx = gpu_context(w, ct=1)
+    ctx.imex_step(30)
+    Ug, Vg = (x.cpu().numpy() for x in ctx.get_state())
+    assert ctx.inst_status()[0] == 0
+    compare_bitwise(Ug, U, "blast U")
+    compare_bitwise(Vg, V, "blast V")
+    compare_bitwise(ctx.get_face_field().cpu().numpy(), b, "blast face field")
+    assert ctx.get_times()[0][0] == t

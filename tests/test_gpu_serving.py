@@ -40,8 +40,8 @@ def grid_of(g):
     return rrmhd.make_grid(g["ndim"], g["n"], g["dx"], g["bc"])
 
 
-def run_alone(req, precision, lanes=1):
-    srv = rrmhd.Server(gamma=GAMMA, precision=precision, lanes=lanes, mem_bytes=1 << 28)
+def run_alone(req, precision, lanes=1, ct=0):
+    srv = rrmhd.Server(gamma=GAMMA, precision=precision, lanes=lanes, mem_bytes=1 << 28, ct=ct)
     g, V, k, s, te = req
     srv.submit(grid_of(g), V, k, s, te)
     srv.wait_idle(120)
@@ -50,9 +50,9 @@ def run_alone(req, precision, lanes=1):
     return res, out
 
 
-def run_context(req, precision):
+def run_context(req, precision, ct=0):
     g, V, k, s, te = req
-    ctx = rrmhd.Context([grid_of(g)], gamma=GAMMA, precision=precision, lanes=1)
+    ctx = rrmhd.Context([grid_of(g)], gamma=GAMMA, precision=precision, lanes=1, ct=ct)
     ctx.set_opacity(torch.tensor(k, device="cuda"), torch.tensor(s, device="cuda"))
     ctx.set_state(torch.tensor(V, device="cuda"))
     ctx.set_times(np.zeros(1), np.array([te]))
@@ -120,6 +120,73 @@ def test_alone_equals_mix(precision):
     for j in (6, 17):
         aj, dj = spans[j]
         assert aj < d0 and a0 < dj
+
+
+def ct_requests(n, seed):
+    """Small requests, planar 2D ones first (constrained transport applies to them)."""
+    reqs = small_requests(n, seed)
+    return sorted(reqs, key=lambda r: -r[0]["ndim"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_server_ct_matches_context_path(precision):
+    """Constrained transport in the server: the face field built at admission and
+    carried through the steps gives the context's result bit for bit."""
+    reqs = ct_requests(8, seed=17)
+    assert reqs[0][0]["ndim"] == 2 and reqs[-1][0]["ndim"] == 1
+    for req in (reqs[0], reqs[1], reqs[-1]):
+        res, out = run_alone(req, precision, ct=1)
+        Vc, tc, stc = run_context(req, precision, ct=1)
+        assert res["status"] == stc
+        compare_bitwise(out, Vc, "server vs context, constrained transport")
+        if req[0]["ndim"] == 2 and stc == 0:
+            _, out0 = run_alone(req, precision, ct=0)
+            assert not np.array_equal(out, out0)   # CT changes the 2D update
+
+
+def test_server_ct_matches_oracle_fp64():
+    import oracle as O
+    req = ct_requests(8, seed=17)[2]     # planar 2D, 19^2 cells, 4 steps
+    g, V, k, s, te = req
+    assert g["ndim"] == 2
+    res, out = run_alone(req, "fp64", ct=1)
+    P = O.Params(gamma=GAMMA, a_rad=1.0, cfl=0.4)
+    og = oracle_grid(g)
+    Vo = np.ascontiguousarray(V).copy()
+    b = O.ct_faces_from_cells(og, Vo)
+    O.ct_canonical(og, b)
+    O.ct_cells_from_faces(og, b, np.zeros_like(Vo), Vo)
+    U = O.prim2con(Vo, P)
+    t, steps, nfail = O.run(og, 0.0, te, U, Vo, k, s, P, max_steps=20000, bface=b)
+    assert (res["status"] == 0) == (nfail == 0)
+    assert res["steps"] == steps and res["t"] == t
+    compare_bitwise(out, Vo, "server (constrained transport) vs oracle")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_ct_alone_equals_mix(precision):
+    """Constrained transport under repacks: the face fields of the survivors move
+    with them; every result equals the request run alone."""
+    reqs = ct_requests(12, seed=19)
+    alone = [run_alone(r, precision, ct=1) for r in reqs]
+    srv = rrmhd.Server(gamma=GAMMA, precision=precision, lanes=3, mem_bytes=1 << 28, ct=1)
+    ids = {}
+    order = list(range(len(reqs)))[::-1]     # 1D ones first, 2D ones join a running batch
+    for w0, w1, pause in [(0, 4, 0.05), (4, 8, 0.05), (8, 12, 0.0)]:
+        for j in order[w0:w1]:
+            g, V, k, s, te = reqs[j]
+            ids[srv.submit(grid_of(g), V, k, s, te)] = j
+        time.sleep(pause)
+    srv.wait_idle(300)
+    got = srv.poll()
+    st = srv.stats()
+    srv.close()
+    assert len(got) == len(reqs) and st["relayouts"] >= 2
+    for res, out in got:
+        j = ids[res["id"]]
+        ra, oa = alone[j]
+        assert res["status"] == ra["status"] and res["steps"] == ra["steps"] and res["t"] == ra["t"]
+        compare_bitwise(out, oa, f"request {j} mixed vs alone (constrained transport)")
 
 
 def test_admission_by_memory_bound():
