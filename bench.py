@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 # measured with ncu on a 2048-instance sample of the same distribution
 # (profiles/c1_k_cells_k_faces_counters.md).
 FP64_INST_PER_ZONE = {"fp64": {"faces": 5640.0, "cells": 5439.0},
-                      "fp32_bulk": {"faces": None, "cells": 4536.0},
+                      "fp32_bulk": {"faces": 4.0, "cells": 4536.0},
                       "fp64_tangent": {"faces": 5249.0, "cells": 5278.0}}
 # DRAM bytes per cell of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
 TRAFFIC_PER_CELL = {"fp64": {"faces": 244.0, "cells": 1009.0},
@@ -73,6 +73,8 @@ def parse():
                    help="requests of the C4 serving sample (0: skip the serving measurement)")
     p.add_argument("--serve-cells", type=int, default=4_000_000,
                    help="resident-cell bound of the serving loop (bounds its step time)")
+    p.add_argument("--no-others", action="store_true",
+                   help="skip the per-step timings of the other workloads (C0 shock tube, 2D blast, 3D box)")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default launch shapes instead of autotuning them before timing")
     p.add_argument("--tuning", default=None,
@@ -266,6 +268,14 @@ def measure(a, precision, rank, world, local):
                       "fallback": round(prof[2] / 3.0, 4), "step_control": round(prof[3] / 2.0, 4)},
         "hbm_frac": BYTES_PER_ZONE_STEP * value / (6791.7e9),
     }
+    # the same FP64 instruction counts over the live, lane-overlapped timed region:
+    # (faces + cells) per zone and stage x 3 stages x zone-updates/s, per GPU
+    live_rate = 3.0 * ((counts.get("faces") or 0.0) + counts["cells"]) * value / max(world, 1)
+    roofline["live_achieved"] = live_rate
+    roofline["live_frac"] = live_rate / FP64_PEAK_INST
+    roofline["live_note"] = ("FP64-pipe instructions of the step's face and cell kernels per "
+                             "zone-update x zone-updates/s of the timed region, per GPU; the "
+                             "whole-batch launch above also carries its tail of slow solves")
 
     e2e = None
     if not a.no_e2e:
@@ -370,11 +380,66 @@ def measure_accuracy(a, n_inst=256, steps=5):
             "note": "FP64 form = the oracle bit for bit; bound 1e-5 per variable"}
 
 
+def measure_workload(w, precision, steps, ct=0, warmup=2):
+    """Per-step device times (CUDA events) of one workload in one context: zone-updates/s
+    over the timed steps and p50/p99 of the step time.  Steps stop at t_end."""
+    import torch
+
+    from paper_2212_00370_gb300 import rrmhd
+
+    grids = [rrmhd.make_grid(g["ndim"], g["n"], g["dx"], g["bc"]) for g in w.grids]
+    ctx = rrmhd.Context(grids, gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl, precision=precision, ct=ct,
+                        lanes=1)
+    ctx.set_opacity(torch.tensor(w.kappa, device="cuda"), torch.tensor(w.sigma, device="cuda"))
+    ctx.set_state(torch.tensor(w.V, device="cuda"))
+    ctx.set_times(np.zeros(w.n_inst), w.t_end)
+    stream = torch.cuda.current_stream()
+    ctx.imex_step(warmup)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        t_before = ctx.get_times()[0]
+        if np.all(t_before >= w.t_end) or np.any(ctx.inst_status() != 0):
+            break
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.imex_step(1)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    st = ctx.inst_status()
+    ctx.close()
+    torch.cuda.empty_cache()
+    if not ms:
+        return {"steps": 0, "status": st.tolist()}
+    return {"value": w.ncells * 1e3 * len(ms) / sum(ms), "unit": "zone-updates/s", "steps": len(ms),
+            "ms_per_step": sum(ms) / len(ms), "p50_ms": float(np.percentile(ms, 50)),
+            "p99_ms": float(np.percentile(ms, 99)), "cells": int(w.ncells), "precision": precision,
+            "ct": ct, "status": int(st.max())}
+
+
+def measure_others():
+    """The other benchmark workloads, each in its own context: the C0 radiative shock
+    tube (400 cells, FP64) to t_end = 0.4 after 2 warm-up steps; the 2D 1024^2 blast
+    (FP32-bulk, constrained transport) and the 3D 256^3 box (FP32-bulk and FP64,
+    constrained transport) over a few steps."""
+    from paper_2212_00370_gb300 import workloads as W
+    out = {}
+    out["shock_tube_400_fp64"] = measure_workload(W.shock_tube(400), "fp64", 1000)
+    c2 = W.blast_2d()
+    out["blast_2d_1024x1024_fp32_bulk_ct"] = measure_workload(c2, "fp32_bulk", 20, ct=1)
+    c3 = W.turbulent_3d()
+    out["box_3d_256cubed_fp32_bulk_ct"] = measure_workload(c3, "fp32_bulk", 5, ct=1)
+    out["box_3d_256cubed_fp64_ct"] = measure_workload(c3, "fp64", 3, ct=1)
+    return out
+
+
 def measure_serving(a, tuning=None):
     """C4 serving sample: the first `serve_requests` requests of the C4 arrival process
     (Poisson, 200 requests/s; 70 % 1D N~U{256..4096}, 30 % planar 2D side~U{128..512};
-    C1 states; t_end 0.2; FP32-bulk) submitted at their arrival times from a host
-    thread into the serving loop, which runs them to completion."""
+    C1 states; t_end 0.2; FP32-bulk, constrained transport for the 2D requests)
+    submitted at their arrival times from a host thread into the serving loop, which
+    runs them to completion."""
     from paper_2212_00370_gb300 import rrmhd
     from paper_2212_00370_gb300 import workloads as W
 
@@ -390,7 +455,7 @@ def measure_serving(a, tuning=None):
     all_specs = W.serving_requests(12000, rate=rate)
     offered = sum(zu_max(sp) for sp in all_specs) / all_specs[-1]["arrival"]
 
-    srv = rrmhd.Server(gamma=4.0 / 3.0, precision="fp32_bulk", lanes=a.lanes,
+    srv = rrmhd.Server(gamma=4.0 / 3.0, precision="fp32_bulk", lanes=a.lanes, ct=1,
                        max_resident_cells=a.serve_cells, tuning=tuning)
     srv.wait_idle(1.0)
 
@@ -419,7 +484,7 @@ def measure_serving(a, tuning=None):
     span = max(r["done_s"] for r, _ in results) - min(r["submit_s"] for r, _ in results)
     return {
         "workload": "C4 sample: first %d requests of Poisson arrivals at %.0f/s (70%% 1D N~U{256..4096}, "
-                    "30%% planar 2D side~U{128..512}, C1 states, t_end 0.2, FP32-bulk)" % (n_req, rate),
+                    "30%% planar 2D side~U{128..512}, C1 states, t_end 0.2, FP32-bulk, CT for 2D)" % (n_req, rate),
         "requests": n_req, "completed": len(results), "failed": len(results) - len(ok),
         "p50_tts_s": float(np.percentile(tts, 50)) if len(tts) else None,
         "p99_tts_s": float(np.percentile(tts, 99)) if len(tts) else None,
@@ -490,6 +555,8 @@ def run_ours(a, rank, world, pool, cores):
         variants["note"] = ("FP64 zone-updates/s of Rad-HLL (Sec. 3.2.1) and PVM-int-16 on the "
                             "C1 batch; the paper reports PVM-int-8 costing ~2x HLL in CPU time")
         out["fp64_variants"] = variants
+    if not a.no_others and world == 1:
+        out["other_workloads"] = measure_others()
     if a.serve_requests > 0 and world == 1:
         out["serving"] = measure_serving(a, res["fp32_bulk"]["tuning"] if "fp32_bulk" in res else None)
     if rank == 0 and pool is not None:
