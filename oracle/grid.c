@@ -201,8 +201,9 @@ int or_grid_stage_c(const or_params* P, const or_grid* g, int stage, double dt,
 
 /* One stage with constrained transport when b0 is not NULL (2D/3D): the face
  * fluxes take the normal field from bs, the staggered field advances to bout
- * (ct.c), the cell-centred B of U* is the mean of bout's faces, and the
- * admissibility fallback replaces all but the magnetic fluxes. */
+ * (ct.c), and the cell-centred B of U* is the mean of bout's faces.  The
+ * admissibility fallback's Rusanov fluxes enter the edge EMFs as well, and bout
+ * is recomputed after each of its passes. */
 int or_grid_stage_ct(const or_params* P, const or_grid* g, int stage, double dt,
                      const double* U0, const double* Us, const double* Vs,
                      const double* kappa, const double* sigma,
@@ -279,18 +280,37 @@ int or_grid_stage_ct(const or_params* P, const or_grid* g, int stage, double dt,
                         load(Vs, N, cr, vr);
                         or_llf_flux(P, d, vl, vr, F);
                         int64_t fi = ((int64_t)k * s.m[d][1] + j) * s.m[d][0] + i;
-                        for (int q = 0; q < 12; q++)
-                            if (!ct || q < 5 || q > 7) s.Fh[d][q * NF + fi] = F[q];
+                        for (int q = 0; q < 12; q++) s.Fh[d][q * NF + fi] = F[q];
                     }
         }
+        /* constrained transport: the edge EMFs of those faces go first-order too,
+         * and the stage's face field is recomputed from the new fluxes */
+        if (ct) or_ct_stage(g, stage, dt, s.Fh, Vs, b0, bs, bout);
         /* update again every cell with a changed face: flagged in this pass or
-         * next to such a cell.  A cell that still fails, and was never flagged,
-         * is flagged for the next pass; in the last pass it fails. */
+         * next to such a cell (with constrained transport, every cell of the
+         * 3x3(x3) block around it: the face field changes on all faces that meet
+         * the flagged cell's edges).  A cell that still fails, and was never
+         * flagged, is flagged for the next pass; in the last pass it fails. */
         for (int k = 0; k < g->n[2]; k++)
             for (int j = 0; j < g->n[1]; j++)
                 for (int i = 0; i < g->n[0]; i++) {
                     int64_t c = lin(g, i, j, k);
                     int hit = bad[c] == pass;
+                    if (ct) {
+                        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+                        for (int d = 0; d < g->ndim; d++) { lo[d] = -1; hi[d] = 1; }
+                        for (int dk = lo[2]; dk <= hi[2] && !hit; dk++)
+                            for (int dj = lo[1]; dj <= hi[1] && !hit; dj++)
+                                for (int di = lo[0]; di <= hi[0] && !hit; di++) {
+                                    int p[3] = {i + di, j + dj, k + dk}, q[3], in = 1;
+                                    for (int d = 0; d < 3; d++) {
+                                        /* an outflow ghost cell is not a neighbour */
+                                        if ((p[d] < 0 || p[d] >= g->n[d]) && g->bc[d] != OR_BC_PERIODIC) in = 0;
+                                        q[d] = map_idx(p[d], g->n[d], g->bc[d]);
+                                    }
+                                    if (in && bad[lin(g, q[0], q[1], q[2])] == pass) hit = 1;
+                                }
+                    }
                     for (int d = 0; d < g->ndim && !hit; d++)
                         for (int e = -1; e <= 1; e += 2) {
                             int q[3] = {i, j, k};

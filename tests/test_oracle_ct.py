@@ -202,3 +202,32 @@ def test_planar_problem_reduces_to_1d(ndim, axis, solver, tol):
     err = (np.abs(UN - ref) / scale).max()
     print("CT planar vs 1D (%s), max relative difference %.2e" % (solver, err))
     assert err < tol
+
+
+def test_fallback_under_ct_keeps_the_constraint():
+    """The 2D blast at 48^2 over 40 steps: the admissibility fallback fires (its
+    Rusanov fluxes enter the edge EMFs) and the implicit solve needs the matter
+    form, yet the discrete divergence stays at round-off and the magnetic flux
+    through every lattice plane of the periodic box is unchanged."""
+    from paper_2212_00370_gb300 import workloads as W
+    w = W.blast_2d(48)
+    P = O.Params(gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl)
+    g = periodic_grid((48, 48))
+    V = np.ascontiguousarray(w.V).copy()
+    b = O.ct_faces_from_cells(g, V)
+    O.ct_canonical(g, b)
+    O.ct_cells_from_faces(g, b, np.zeros_like(V), V)
+    U = O.prim2con(V, P)
+    nx = ny = 48
+    fx0 = b[:(nx + 1) * ny].reshape(ny, nx + 1).sum(axis=0)
+    fy0 = b[(nx + 1) * ny:].reshape(ny + 1, nx).sum(axis=1)
+    st = O.Stats()
+    t, steps, nfail = O.run(g, 0.0, np.inf, U, V, w.kappa, w.sigma, P, max_steps=40, stats=st, bface=b)
+    assert nfail == 0 and steps == 40
+    assert st.fallback_cells > 0 and st.imp_matter > 0
+    h = 1.0 / 48
+    assert np.abs(O.ct_div(g, b)).max() * h / np.abs(b).max() < 1e-13
+    fx = b[:(nx + 1) * ny].reshape(ny, nx + 1).sum(axis=0)
+    fy = b[(nx + 1) * ny:].reshape(ny + 1, nx).sum(axis=1)
+    scale = np.abs(b).sum()
+    assert np.abs(fx - fx0).max() <= 1e-13 * scale and np.abs(fy - fy0).max() <= 1e-13 * scale
