@@ -90,6 +90,7 @@ struct StageArgs {
   int32_t* cell_status;    // optional per-cell status
   uint8_t* bad;            // [ncells] fallback flags: p > 0 = flagged in pass p, 0 = not flagged
   int fb_pass;             // the admissibility-fallback pass a fallback launch runs, 1..kFallbackPasses
+                           // (0: the main path)
   unsigned int* flagged;   // [kFallbackPasses + 1]: cells flagged with value p in this stage, or null
   double* jc;              // [17][ncells] per-cell Jacobian cache of the implicit solve
   unsigned long long* work;  // [2] chunk counters of persistent face / cell launches
@@ -119,7 +120,8 @@ struct Tuning {
 // shape needs a.work zeroed on the stream before the launch (the launchers do it).
 void launch_faces_f64(const StageArgs& a, const LaunchShape& sh, cudaStream_t s);
 void launch_cells_f64(const StageArgs& a, const LaunchShape& sh, cudaStream_t s);
-// one pass of the admissibility fallback (a.fb_pass): its faces, then its cells
+// one pass of the admissibility fallback (a.fb_pass): its faces, then (constrained
+// transport) the EMFs and the face field again, then its cells
 void launch_fallback_f64(const StageArgs& a, cudaStream_t s);
 void launch_signal_f64(const Params& P, const Batch& b, const double* V, cudaStream_t s);
 // constrained transport: edge EMFs (CT-contact) and the face-field stage update

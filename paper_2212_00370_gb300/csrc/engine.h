@@ -245,7 +245,7 @@ inline StageArgs stage_args(const Params& P, const DeviceBufs& B, const Batch& b
   a.Vout = Vout;
   a.cell_status = nullptr;
   a.bad = B.bad;
-  a.fb_pass = 1;
+  a.fb_pass = 0;  // the main path; launch_fallback sets its passes
   a.flagged = (cnt && stage >= 1) ? cnt->flagged[stage - 1] : nullptr;
   a.jc = B.jc;
   a.work = cnt ? cnt->work : nullptr;
@@ -284,7 +284,10 @@ inline void launch_fallback(int precision, const StageArgs& a, cudaStream_t s) {
 }
 
 // Kernel launches of one step on one lane.
-inline int launches_per_step(int ct) { return 2 + 3 * (2 + 2 * kFallbackPasses + (ct ? 2 : 0)); }
+// (constrained transport: EMFs and face field in the main path and in every pass)
+inline int launches_per_step(int ct) {
+  return 2 + 3 * (2 + 2 * kFallbackPasses + (ct ? 2 + 2 * kFallbackPasses : 0));
+}
 
 // The launch groups of one stage in the given precision and shapes: faces, then
 // (constrained transport) edge EMFs and the face-field update, cells, fallback.
@@ -309,8 +312,9 @@ inline bool tuning_ok(const Tuning& t) {
 // A = S[cur] into B = S[1-cur], with C = (Ub,Vb) for stage 2:
 // stage 1 A -> B, stage 2 (B; A) -> C, stage 3 (C; A) -> B.  No stage writes its
 // inputs, so the admissibility fallback can re-read them.  Launches: begin,
-// 3 x {faces, [emf, bface,] cells, kFallbackPasses x {fallback faces, fallback
-// cells}}, end (launches_per_step).  The flag counters are zeroed by a memset.
+// 3 x {faces, [emf, bface,] cells, kFallbackPasses x {fallback faces, [emf,
+// bface,] fallback cells}}, end (launches_per_step).  The flag counters are
+// zeroed by a memset.
 // cnt: this stream's counters (persistent shapes, fallback passes).
 // ct: constrained transport on (the face-field sets rotate with the state).
 inline void enqueue_step(const Params& P, int precision, const Tuning& tu, const DeviceBufs& B,

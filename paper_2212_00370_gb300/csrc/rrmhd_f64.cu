@@ -275,10 +275,9 @@ __global__ void __launch_bounds__(kFaceThreads) k_fallback_faces(StageArgs a) {
   load12(a.Vs, b.ncells, cl, vl);
   load12(a.Vs, b.ncells, cr, vr);
   llf_flux(a.P, d, vl, vr, F);
-  const bool keep_b = a.ct && I.ndim >= 2;  // CT: the solver's magnetic fluxes stay
+  // (constrained transport: the magnetic components enter the edge EMFs)
 #pragma unroll
-  for (int k = 0; k < NV; ++k)
-    if (!keep_b || k < 5 || k > 7) a.Fhat[k * a.fstride + g] = F[k];
+  for (int k = 0; k < NV; ++k) a.Fhat[k * a.fstride + g] = F[k];
 }
 
 // Admissibility fallback, pass a.fb_pass, cells: update again every cell with a
@@ -309,6 +308,23 @@ __global__ void __launch_bounds__(kCellThreads, RR_CELL_MIN_BLOCKS) k_fallback_c
   }
   const InstDesc& I = q.I;
   bool hit = !none && a.bad[c] == pass;
+  if (!none && !hit && a.ct && I.ndim >= 2) {
+    // constrained transport: the face field changes on every face that meets a
+    // flagged cell's edges, so the whole 3x3(x3) block around it is updated again
+    const int lo2 = I.ndim == 3 ? -1 : 0, hi2 = I.ndim == 3 ? 1 : 0;
+    for (int dk = lo2; dk <= hi2 && !hit; ++dk)
+      for (int dj = -1; dj <= 1 && !hit; ++dj)
+        for (int di = -1; di <= 1 && !hit; ++di) {
+          const int p[3] = {q.p[0] + di, q.p[1] + dj, q.p[2] + dk};
+          bool in = true;
+          int r[3];
+          for (int d = 0; d < 3; ++d) {
+            if ((p[d] < 0 || p[d] >= I.n[d]) && I.bc[d] != 1) in = false;  // outflow ghost cell
+            r[d] = map_idx(p[d], I.n[d], I.bc[d]);
+          }
+          if (in && a.bad[I.cell_off + ((int64_t)r[2] * I.n[1] + r[1]) * I.n[0] + r[0]] == pass) hit = true;
+        }
+  }
   for (int d = 0; d < I.ndim && !hit && !none; ++d) {
     for (int e = -1; e <= 1; e += 2) {
       const int pd = q.p[d] + e;
@@ -371,6 +387,7 @@ __global__ void __launch_bounds__(kFaceThreads) k_emf(StageArgs a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const Batch& b = a.b;
   if (t >= lane_edges(b)) return;
+  if (a.fb_pass > 0 && a.flagged && a.flagged[a.fb_pass] == 0) return;  // fallback pass: nothing flagged
   const EdgePos q = edge_pos(b, t);
   if (!inst_active(b, q.i)) return;
   const InstDesc& I = q.I;
@@ -414,6 +431,7 @@ __global__ void __launch_bounds__(kFaceThreads) k_bface(StageArgs a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const Batch& b = a.b;
   if (t >= lane_faces(b)) return;
+  if (a.fb_pass > 0 && a.flagged && a.flagged[a.fb_pass] == 0) return;  // fallback pass: nothing flagged
   const int64_t g = lane_face(b, t);
   const FacePos fp = face_pos(b, g);
   const InstDesc& I = fp.I;
@@ -655,6 +673,10 @@ void launch_fallback_f64(const StageArgs& a, cudaStream_t s) {
   const int64_t nf = a.b.f_count[0] + a.b.f_count[1] + a.b.f_count[2];
   const int64_t nc = a.b.c_end - a.b.c_begin;
   if (nf > 0) k_fallback_faces<<<grid_for(nf, kFaceThreads), kFaceThreads, 0, s>>>(a);
+  if (a.ct) {
+    launch_emf_f64(a, s);
+    launch_bface_f64(a, s);
+  }
   if (nc > 0) k_fallback_cells<<<grid_for(nc, kCellThreads), kCellThreads, 0, s>>>(a);
 }
 
