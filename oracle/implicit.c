@@ -291,13 +291,15 @@ static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z,
                         Mout[4 * i + j] = (J[i][j] - (i == j ? 1.0 : 0.0)) / c->hdt;
             return 0;
         }
-        /* backtracking line search: halve the step until the matter state is
-         * admissible and |R|^2 decreases (the initial frozen-matter matrix gets
-         * four halvings before the full Jacobian replaces it) */
+        /* backtracking line search: halve the step, at most ten times, until the
+         * matter state is admissible and |R|^2 decreases (the initial frozen-matter
+         * matrix gets four halvings before the full Jacobian replaces it).  A
+         * direction that needs more is not worth following: the matrix is replaced,
+         * or the continuation in h and the matter form take over. */
         double r0 = ((R[0] * R[0] + R[1] * R[1]) + R[2] * R[2]) + R[3] * R[3];
         double lam = 1.0;
         int ok = 0;
-        for (int k = 0; k < 40; k++) {
+        for (int k = 0; k < 10; k++) {
             for (int i = 0; i < 4; i++) Xn[i] = X[i] + dX[i];
             if (!imp_residual(c, Xn, *Z, Rn, Vn, &Zn)) {
                 double r1 = ((Rn[0] * Rn[0] + Rn[1] * Rn[1]) + Rn[2] * Rn[2]) + Rn[3] * Rn[3];

@@ -336,7 +336,8 @@ __device__ __forceinline__ void picard_matrix(const ImpCell& c, const double* X,
 // Quasi-Newton iteration on R(X) = 0: first matrix C^(m) (the paper's
 // frozen-matter iteration), Broyden rank-one update after every accepted step,
 // forward-difference Jacobian (step 1e-7 E_r) when successive steps contract by
-// less than 2x or no descent is found; Armijo backtracking on |R|^2; converged
+// less than 2x or no descent is found; Armijo backtracking on |R|^2 (at most ten
+// halvings); converged
 // when the full step is <= imp_tol * E_r.  Returns true on convergence.
 static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c, double* X, double* R,
                                         double* V, double* Z, const double* Min, double* Mout) {
@@ -410,7 +411,7 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
     const double r0 = ((R[0] * R[0] + R[1] * R[1]) + R[2] * R[2]) + R[3] * R[3];
     double lam = 1.0;
     int ok = 0;
-    for (int k = 0; k < 40; ++k) {
+    for (int k = 0; k < 10; ++k) {  // at most ten halvings
 #pragma unroll
       for (int i = 0; i < 4; ++i) Xn[i] = X[i] + dX[i];
       if (imp_residual(P, c, Xn, *Z, Rn, Vn, &Zn)) {

@@ -203,8 +203,8 @@ def test_matter_form_agrees_with_the_iteration_on_x():
     Us = O.prim2con(RAD_DOMINATED, Pn)
     Zg = O.prim_Z(RAD_DOMINATED, Pn)
     st = O.Stats()
-    Ux, _, rx = O.implicit(Us, 2.7, 0.0, 1.9e-3, Pn, Zguess=Zg, stats=st)
-    Uy, _, ry = O.implicit(Us, 2.7, 0.0, 1.9e-3, Pm, Zguess=Zg)
+    Ux, _, rx = O.implicit(Us, 2.7, 0.0, 1e-3, Pn, Zguess=Zg, stats=st)
+    Uy, _, ry = O.implicit(Us, 2.7, 0.0, 1e-3, Pm, Zguess=Zg)
     assert rx == 0 and ry == 0 and st.imp_matter == 0
     # within the iteration on X's own bound (imp_tol E_r): its matter part is only
     # good to ~1e-7 here, which is the reason for the matter form
