@@ -204,6 +204,15 @@ __device__ __forceinline__ void c2p_eval(const C2PIn& c, double x, C2PPt& e) {
 }
 
 // Returns a Status; V and *Zout are written only on success.
+// Convergence rule: once a Newton step is <= 1e-10 x, one more step is taken (the
+// finite-difference products of the PVM flux differentiate con2prim, and the fixed
+// extra step keeps the converged value reproducible).  A translation unit that
+// defines RR_C2P_POST_STEP 0 (the FP32-bulk cells, which feed no such product)
+// stops at that step instead: with Newton's quadratic convergence the remaining
+// error is of order (1e-10 x)^2 / x.
+#ifndef RR_C2P_POST_STEP
+#define RR_C2P_POST_STEP 1
+#endif
 static __device__ __noinline__ int con2prim(const Params& P, const double* U, double Zguess, double* V,
                                      double* Zout) {
   C2PIn c;
@@ -248,7 +257,13 @@ static __device__ __noinline__ int con2prim(const Params& P, const double* U, do
       conv = 1;
       break;
     }
-    if (fabs(dx) <= 1e-10 * x) final_step = 1;
+    if (fabs(dx) <= 1e-10 * x) {
+      if (!RR_C2P_POST_STEP) {
+        conv = 1;
+        break;
+      }
+      final_step = 1;
+    }
   }
   if (!conv || !(e.p > 0.0)) return ST_C2P;
   const double rho = c.D / e.W;
