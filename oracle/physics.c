@@ -145,6 +145,9 @@ void or_flux(const or_params* P, int d, const double V[12], const double U[12], 
  * Stopping rule: once |dW'| <= 1e-10 W' the iteration is in its quadratic
  * regime and exactly one more Newton step is taken (the result is then exact
  * to rounding, which the nested flux differences of the PVM flux require).
+ * The cells' recoveries (the implicit solve, or_con2prim_cell) feed no such
+ * difference and stop at that step: Newton's quadratic convergence leaves an
+ * error of order (1e-10 W')^2 / W' there.
  * A step that leaves the admissible region (W' <= 0 or v^2 >= 1) is halved.
  * ---------------------------------------------------------------------- */
 typedef struct {
@@ -188,8 +191,8 @@ static void c2p_eval(const c2p_in* c, double x, c2p_pt* e)
     e->ok = 1;
 }
 
-int or_con2prim(const or_params* P, const double U[12], double Zguess,
-                double V[12], double* Zout, or_stats* st)
+static int c2p_solve(const or_params* P, const double U[12], double Zguess,
+                     double V[12], double* Zout, or_stats* st, int post_step)
 {
     c2p_in c;
     c.D = U[0];
@@ -235,7 +238,10 @@ int or_con2prim(const or_params* P, const double U[12], double Zguess,
         x = en.x;
         e = en;
         if (final) { conv = 1; break; }
-        if (fabs(dx) <= 1e-10 * x) final = 1;
+        if (fabs(dx) <= 1e-10 * x) {
+            if (!post_step) { conv = 1; break; }
+            final = 1;
+        }
     }
     if (!conv || !(e.p > 0.0)) {
         if (st) st->c2p_fail++;
@@ -253,6 +259,18 @@ int or_con2prim(const or_params* P, const double U[12], double Zguess,
     }
     if (Zout) *Zout = e.Z;
     return OR_OK;
+}
+
+int or_con2prim(const or_params* P, const double U[12], double Zguess,
+                double V[12], double* Zout, or_stats* st)
+{
+    return c2p_solve(P, U, Zguess, V, Zout, st, 1);
+}
+
+int or_con2prim_cell(const or_params* P, const double U[12], double Zguess,
+                     double V[12], double* Zout, or_stats* st)
+{
+    return c2p_solve(P, U, Zguess, V, Zout, st, 0);
 }
 
 /* Largest |signal speed| of a cell along direction d, capped at 1 (c = 1).

@@ -205,16 +205,13 @@ __device__ __forceinline__ void c2p_eval(const C2PIn& c, double x, C2PPt& e) {
 
 // Returns a Status; V and *Zout are written only on success.
 // Convergence rule: once a Newton step is <= 1e-10 x, one more step is taken (the
-// finite-difference products of the PVM flux differentiate con2prim, and the fixed
-// extra step keeps the converged value reproducible).  A translation unit that
-// defines RR_C2P_POST_STEP 0 (the FP32-bulk cells, which feed no such product)
-// stops at that step instead: with Newton's quadratic convergence the remaining
-// error is of order (1e-10 x)^2 / x.
-#ifndef RR_C2P_POST_STEP
-#define RR_C2P_POST_STEP 1
-#endif
-static __device__ __noinline__ int con2prim(const Params& P, const double* U, double Zguess, double* V,
-                                     double* Zout) {
+// finite-difference products of the PVM flux differentiate con2prim, and the extra
+// step makes the result exact to rounding).  con2prim_cell, used by the cells'
+// implicit solve, which feeds no such difference, stops at that step: Newton's
+// quadratic convergence leaves an error of order (1e-10 x)^2 / x there.
+template <int kPostStep>
+static __device__ __noinline__ int con2prim_solve(const Params& P, const double* U, double Zguess,
+                                                  double* V, double* Zout) {
   C2PIn c;
   c.D = U[0];
   c.S[0] = U[1];
@@ -258,7 +255,7 @@ static __device__ __noinline__ int con2prim(const Params& P, const double* U, do
       break;
     }
     if (fabs(dx) <= 1e-10 * x) {
-      if (!RR_C2P_POST_STEP) {
+      if (!kPostStep) {
         conv = 1;
         break;
       }
@@ -277,6 +274,16 @@ static __device__ __noinline__ int con2prim(const Params& P, const double* U, do
   for (int k = 5; k < NV; ++k) V[k] = U[k];
   if (Zout) *Zout = e.Z;
   return ST_OK;
+}
+
+__device__ __forceinline__ int con2prim(const Params& P, const double* U, double Zguess, double* V,
+                                        double* Zout) {
+  return con2prim_solve<1>(P, U, Zguess, V, Zout);
+}
+
+__device__ __forceinline__ int con2prim_cell(const Params& P, const double* U, double Zguess,
+                                             double* V, double* Zout) {
+  return con2prim_solve<0>(P, U, Zguess, V, Zout);
 }
 
 // ------------------------------------------------------------- signal speed

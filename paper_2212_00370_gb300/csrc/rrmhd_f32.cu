@@ -5,10 +5,6 @@
 // radiation-matter solve and the accumulation of U stay in FP64 (the same solver
 // as the FP64 path, compiled here with fused multiply-add).  Same launch
 // structure and lanes as rrmhd_f64.cu.
-// The cells' con2prim stops at the first Newton step below its tolerance (no
-// post-convergence step: nothing here differentiates it by finite differences
-// at the 1e-8 level).
-#define RR_C2P_POST_STEP 0
 #include <cuda_runtime.h>
 
 #include "batch.h"
