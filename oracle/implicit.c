@@ -60,7 +60,7 @@ static int imp_residual(imp_ctx* c, const double X[4], double Zg, double R[4],
     if (c->st) c->st->imp_resid++;
     if (!(X[0] > 0.0)) return 1;
     matter_state(c, X, Um);
-    if (or_con2prim_cell(c->P, Um, Zg, V, Z, c->st) != OR_OK) return 1;
+    if (or_con2prim(c->P, Um, Zg, V, Z, c->st) != OR_OK) return 1;
     double v2 = (V[1] * V[1] + V[2] * V[2]) + V[3] * V[3];
     double W = 1.0 / sqrt(1.0 - v2);
     double u[3] = {W * V[1], W * V[2], W * V[3]};
@@ -199,7 +199,7 @@ static int picard(imp_ctx* c, double X[4], double V[12], double* Z)
         }
         if (!(X[0] > 0.0)) return 1;
         matter_state(c, X, Um);
-        if (or_con2prim_cell(P, Um, *Z, V, Z, c->st) != OR_OK) return 1;
+        if (or_con2prim(P, Um, *Z, V, Z, c->st) != OR_OK) return 1;
         if (dmax <= P->imp_tol * X[0]) return 0;
     }
     return 1;
@@ -438,7 +438,7 @@ static int implicit_cell(const or_params* P, double kappa, double sigma, double 
     if (st) st->imp_cells++;
     if ((kappa == 0.0 && sigma == 0.0) || hdt == 0.0) {
         for (int k = 0; k < 12; k++) U[k] = Ustar[k];
-        int rc = or_con2prim_cell(P, Ustar, Zguess, V, 0, st);
+        int rc = or_con2prim(P, Ustar, Zguess, V, 0, st);
         if (rc != OR_OK && st) st->imp_fail++;
         return rc;
     }

@@ -82,9 +82,6 @@ void   or_m1_pressure(double E, const double F[3], double Pr[3][3]);
 double or_eddington_factor(double f);
 int    or_con2prim(const or_params* P, const double U[12], double Zguess,
                    double V[12], double* Zout, or_stats* st);
-/* the same recovery without the post-convergence step (the cells' implicit solve) */
-int    or_con2prim_cell(const or_params* P, const double U[12], double Zguess,
-                        double V[12], double* Zout, or_stats* st);
 double or_signal_speed(const or_params* P, int dir, const double V[12]);
 void   or_four_force(double kappa, double sigma, double rho, const double u[3], double W,
                      double BP, double E, const double F[3], const double Pr[3][3], double G[4]);

@@ -142,12 +142,11 @@ void or_flux(const or_params* P, int d, const double V[12], const double U[12], 
  *   p(W')  = (gamma-1)/gamma [ W' (1 - v^2) - D v^2/(W + 1) ]
  *   f(W')  = W' - p + B^2 (1 + v^2)/2 - (S.B)^2/(2 Z^2) - tau_e = 0
  *   v^i    = (S^i + (S.B) B^i / Z) / (Z + B^2),   rho = D / W.
- * Stopping rule: once |dW'| <= 1e-10 W' the iteration is in its quadratic
- * regime and exactly one more Newton step is taken (the result is then exact
- * to rounding, which the nested flux differences of the PVM flux require).
- * The cells' recoveries (the implicit solve, or_con2prim_cell) feed no such
- * difference and stop at that step: Newton's quadratic convergence leaves an
- * error of order (1e-10 W')^2 / W' there.
+ * Stopping rule: the iteration stops at the Newton step with |dW'| <= 1e-10 W'
+ * (the step is taken).  In Newton's quadratic regime the error left is of
+ * order (1e-10 W')^2 / W', below rounding, so the nested flux differences of
+ * the PVM flux, which differentiate con2prim at the 1e-8 level, see a
+ * recovery exact to rounding.
  * A step that leaves the admissible region (W' <= 0 or v^2 >= 1) is halved.
  * ---------------------------------------------------------------------- */
 typedef struct {
@@ -191,8 +190,8 @@ static void c2p_eval(const c2p_in* c, double x, c2p_pt* e)
     e->ok = 1;
 }
 
-static int c2p_solve(const or_params* P, const double U[12], double Zguess,
-                     double V[12], double* Zout, or_stats* st, int post_step)
+int or_con2prim(const or_params* P, const double U[12], double Zguess,
+                double V[12], double* Zout, or_stats* st)
 {
     c2p_in c;
     c.D = U[0];
@@ -224,7 +223,7 @@ static int c2p_solve(const or_params* P, const double U[12], double Zguess,
         return OR_EC2P;
     }
 
-    int final = 0, conv = 0;
+    int conv = 0;
     for (int it = 1; it <= P->c2p_maxit; it++) {
         double dx = -e.f / e.df;
         c2p_pt en;
@@ -237,11 +236,7 @@ static int c2p_solve(const or_params* P, const double U[12], double Zguess,
         if (!en.ok) break;
         x = en.x;
         e = en;
-        if (final) { conv = 1; break; }
-        if (fabs(dx) <= 1e-10 * x) {
-            if (!post_step) { conv = 1; break; }
-            final = 1;
-        }
+        if (fabs(dx) <= 1e-10 * x) { conv = 1; break; }
     }
     if (!conv || !(e.p > 0.0)) {
         if (st) st->c2p_fail++;
@@ -259,18 +254,6 @@ static int c2p_solve(const or_params* P, const double U[12], double Zguess,
     }
     if (Zout) *Zout = e.Z;
     return OR_OK;
-}
-
-int or_con2prim(const or_params* P, const double U[12], double Zguess,
-                double V[12], double* Zout, or_stats* st)
-{
-    return c2p_solve(P, U, Zguess, V, Zout, st, 1);
-}
-
-int or_con2prim_cell(const or_params* P, const double U[12], double Zguess,
-                     double V[12], double* Zout, or_stats* st)
-{
-    return c2p_solve(P, U, Zguess, V, Zout, st, 0);
 }
 
 /* Largest |signal speed| of a cell along direction d, capped at 1 (c = 1).

@@ -204,14 +204,12 @@ __device__ __forceinline__ void c2p_eval(const C2PIn& c, double x, C2PPt& e) {
 }
 
 // Returns a Status; V and *Zout are written only on success.
-// Convergence rule: once a Newton step is <= 1e-10 x, one more step is taken (the
-// finite-difference products of the PVM flux differentiate con2prim, and the extra
-// step makes the result exact to rounding).  con2prim_cell, used by the cells'
-// implicit solve, which feeds no such difference, stops at that step: Newton's
-// quadratic convergence leaves an error of order (1e-10 x)^2 / x there.
-template <int kPostStep>
-static __device__ __noinline__ int con2prim_solve(const Params& P, const double* U, double Zguess,
-                                                  double* V, double* Zout) {
+// Stopping rule: the iteration stops at the Newton step with |dx| <= 1e-10 x (the
+// step is taken).  In Newton's quadratic regime the error left is of order
+// (1e-10 x)^2 / x, below rounding, so the PVM's finite-difference products, which
+// differentiate con2prim at the 1e-8 level, see a recovery exact to rounding.
+static __device__ __noinline__ int con2prim(const Params& P, const double* U, double Zguess,
+                                            double* V, double* Zout) {
   C2PIn c;
   c.D = U[0];
   c.S[0] = U[1];
@@ -238,7 +236,7 @@ static __device__ __noinline__ int con2prim_solve(const Params& P, const double*
   }
   if (!e.ok) return ST_C2P;
 
-  int final_step = 0, conv = 0;
+  int conv = 0;
   for (int it = 1; it <= P.c2p_maxit; ++it) {
     double dx = -e.f / e.df;
     C2PPt en;
@@ -250,16 +248,9 @@ static __device__ __noinline__ int con2prim_solve(const Params& P, const double*
     if (!en.ok) break;
     x = en.x;
     e = en;
-    if (final_step) {
+    if (fabs(dx) <= 1e-10 * x) {
       conv = 1;
       break;
-    }
-    if (fabs(dx) <= 1e-10 * x) {
-      if (!kPostStep) {
-        conv = 1;
-        break;
-      }
-      final_step = 1;
     }
   }
   if (!conv || !(e.p > 0.0)) return ST_C2P;
@@ -274,16 +265,6 @@ static __device__ __noinline__ int con2prim_solve(const Params& P, const double*
   for (int k = 5; k < NV; ++k) V[k] = U[k];
   if (Zout) *Zout = e.Z;
   return ST_OK;
-}
-
-__device__ __forceinline__ int con2prim(const Params& P, const double* U, double Zguess, double* V,
-                                        double* Zout) {
-  return con2prim_solve<1>(P, U, Zguess, V, Zout);
-}
-
-__device__ __forceinline__ int con2prim_cell(const Params& P, const double* U, double Zguess,
-                                             double* V, double* Zout) {
-  return con2prim_solve<0>(P, U, Zguess, V, Zout);
 }
 
 // ------------------------------------------------------------- signal speed

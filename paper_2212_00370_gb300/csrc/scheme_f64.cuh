@@ -244,7 +244,7 @@ static __device__ __noinline__ bool imp_residual(const Params& P, const ImpCell&
   if (!(X[0] > 0.0)) return false;
   double Um[NV];
   matter_state(c, X, Um);
-  if (con2prim_cell(P, Um, Zg, V, Z) != ST_OK) return false;
+  if (con2prim(P, Um, Zg, V, Z) != ST_OK) return false;
   const double v2 = (V[1] * V[1] + V[2] * V[2]) + V[3] * V[3];
   const double W = 1.0 / sqrt(1.0 - v2);
   const double u[3] = {W * V[1], W * V[2], W * V[3]};
@@ -609,7 +609,7 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
   if ((kappa == 0.0 && sigma == 0.0) || hdt == 0.0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) U[k] = Us[k];
-    return con2prim_cell(P, Us, Zguess, V, nullptr);
+    return con2prim(P, Us, Zguess, V, nullptr);
   }
   ImpCell c;
   c.kappa = kappa;
