@@ -41,13 +41,13 @@ sys.path.insert(0, ROOT)
 # of each kernel in the steady state of this workload (stage 1 of the 4th step),
 # measured with ncu on a 2048-instance sample of the same distribution
 # (profiles/c1_k_cells_k_faces_counters.md).
-FP64_INST_PER_ZONE = {"fp64": {"faces": 5731.0, "cells": 4600.0},
+FP64_INST_PER_ZONE = {"fp64": {"faces": 4831.0, "cells": 4576.0},
                       "fp32_bulk": {"faces": 4.0, "cells": 3716.0},
-                      "fp64_tangent": {"faces": 5334.0, "cells": 4597.0}}
+                      "fp64_tangent": {"faces": 5239.0, "cells": 4597.0}}
 # DRAM bytes per cell of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
-TRAFFIC_PER_CELL = {"fp64": {"faces": 253.0, "cells": 1196.0},
-                    "fp32_bulk": {"faces": 176.0, "cells": 1175.0},
-                    "fp64_tangent": {"faces": 240.0, "cells": 1202.0}}
+TRAFFIC_PER_CELL = {"fp64": {"faces": 250.0, "cells": 1203.0},
+                    "fp32_bulk": {"faces": 176.0, "cells": 1174.0},
+                    "fp64_tangent": {"faces": 240.0, "cells": 1200.0}}
 # Nominal FP64 rate of GB300: 1.25 TFLOP/s = 6.25e11 FP64-pipe instructions/s
 # (2 per SM per clock on 152 SMs at 2.07 GHz); no MEASURED_PEAKS entry exists for FP64.
 FP64_PEAK_INST = 6.25e11
