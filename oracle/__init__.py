@@ -381,7 +381,7 @@ def stage(g, s, dt, U0, Us, Vs, kappa, sigma, P, stats=None):
 
 def step(g, dt, U, V, kappa, sigma, P, stats=None, jcache=None, bface=None):
     """One IMEX-RK3 step in place; returns the number of failed cells.  jcache: a
-    float64 array of 21 * ncells (zeros = empty) carried between steps, or None.
+    float64 array of 17 * ncells (zeros = empty) carried between steps, or None.
     bface: the staggered field of constrained transport (2D/3D; ct_nfaces(g)
     values, advanced in place), or None."""
     N = g.ncells
@@ -393,8 +393,8 @@ def step(g, dt, U, V, kappa, sigma, P, stats=None, jcache=None, bface=None):
         return lib().or_grid_step(C.byref(P.struct()), C.byref(g.struct()), float(dt), _d(U),
                                   _d(V), _d(k), _d(s), _stats(stats))
     if jcache is None:
-        jcache = np.zeros(21 * N)
-    assert jcache.size == 21 * N and jcache.dtype == np.float64 and jcache.flags.c_contiguous
+        jcache = np.zeros(17 * N)
+    assert jcache.size == 17 * N and jcache.dtype == np.float64 and jcache.flags.c_contiguous
     if bface is None:
         return lib().or_grid_step_c(C.byref(P.struct()), C.byref(g.struct()), float(dt), _d(U),
                                     _d(V), _d(k), _d(s), _d(jcache), _stats(stats))

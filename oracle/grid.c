@@ -125,7 +125,7 @@ typedef struct {
     double* Fh[3];
     int m[3][3];
     const double *U0, *Us, *Vs, *kappa, *sigma;
-    double* jc;   /* per-cell cache of the implicit solve, [OR_JC_PLANES][N], or NULL */
+    double* jc;   /* per-cell Jacobian cache, [17][N] planes, or NULL */
     const double* bface;   /* the stage's new staggered field (constrained transport), or NULL */
 } stage_ctx;
 
@@ -162,10 +162,10 @@ static int cell_update(const stage_ctx* s, int i, int j, int k, double Un[12], d
     load(s->Vs, N, c, vs);
     double Zg = or_prim_Z(s->P, vs);
     if (!s->jc) return or_implicit(s->P, s->kappa[c], s->sigma[c], s->hdt, Ust, Zg, Un, Vn, st);
-    double jc[OR_JC_PLANES];
-    for (int q = 0; q < OR_JC_PLANES; q++) jc[q] = s->jc[q * N + c];
+    double jc[17];
+    for (int q = 0; q < 17; q++) jc[q] = s->jc[q * N + c];
     int rc = or_implicit_c(s->P, s->kappa[c], s->sigma[c], s->hdt, Ust, Zg, Un, Vn, jc, st);
-    for (int q = 0; q < OR_JC_PLANES; q++) s->jc[q * N + c] = jc[q];
+    for (int q = 0; q < 17; q++) s->jc[q * N + c] = jc[q];
     return rc;
 }
 
@@ -354,8 +354,7 @@ int or_grid_stage(const or_params* P, const or_grid* g, int stage, double dt,
 }
 
 /* One full IMEX-RK3 step of size dt; U and V are updated in place.  jcache: the
- * per-cell cache of the implicit solve carried from step to step ([OR_JC_PLANES][N],
- * zero = empty), or NULL. */
+ * per-cell Jacobian cache carried from step to step ([17][N], zero = empty), or NULL. */
 int or_grid_step_c(const or_params* P, const or_grid* g, double dt, double* U, double* V,
                    const double* kappa, const double* sigma, double* jcache, or_stats* st)
 {
@@ -422,7 +421,7 @@ int or_grid_run_ct(const or_params* P, const or_grid* g, double t0, double t_end
 {
     double t = t0;
     int s = 0, nfail = 0;
-    double* jc = (double*)calloc((size_t)OR_JC_PLANES * ncells(g), sizeof(double));
+    double* jc = (double*)calloc((size_t)17 * ncells(g), sizeof(double));
     while (t < t_end && s < max_steps) {
         double dt = or_grid_dt(P, g, V);
         if (t + dt > t_end) dt = t_end - t;

@@ -423,13 +423,8 @@ static int solve_matter(imp_ctx* c, const double Vs[12], double X[4], double V[1
     return newton_m(c, Y, X, V);
 }
 
-/* Predictor: a cell whose last solve converged on X (flag 1) starts from
- * X* + h D, D its last correction per unit weight, with its cached matrix; the
- * residual at X* is then not needed.  If that admissible start does not
- * converge, the solve starts over from X* as below.
- *
- * jc (may be NULL): the cell's cache, OR_JC_PLANES entries: M = (J - I)/h from its
- * last converged solve (16), a validity flag jc[16] and D = (X - X*)/h (4).  A valid entry is the first
+/* jc (may be NULL): the cell's Jacobian cache, 16 entries of M = (J - I)/h from its
+ * last converged solve and a validity flag jc[16].  A valid entry is the first
  * matrix of the quasi-Newton iteration instead of C^(m); the converged matrix is
  * stored back (the flag is cleared when the solve fails).  M does not depend on h,
  * so it carries over between stages of different weight.  Flag 2 records that the
@@ -463,16 +458,6 @@ static int implicit_cell(const or_params* P, double kappa, double sigma, double 
 
     double X[4] = {c.Xs[0], c.Xs[1], c.Xs[2], c.Xs[3]};
     double R[4], Z = Zguess;
-    if (jc && jc[16] == 1.0 && P->imp_mode == OR_IMP_NEWTON) {
-        double Xp[4], Zp = Zguess, Mp[16];
-        for (int i = 0; i < 4; i++) Xp[i] = c.Xs[i] + hdt * jc[17 + i];
-        if (!imp_residual(&c, Xp, Zguess, R, V, &Zp) && !newton(&c, Xp, R, V, &Zp, jc, Mp)) {
-            for (int k = 0; k < 16; k++) jc[k] = Mp[k];
-            for (int i = 0; i < 4; i++) jc[17 + i] = (Xp[i] - c.Xs[i]) / hdt;
-            matter_state(&c, Xp, U);
-            return OR_OK;
-        }
-    }
     int fail = imp_residual(&c, X, Zguess, R, V, &Z);
     if (fail) {
         /* the explicit state U* itself is inadmissible (no con2prim root or E_r <= 0) */
@@ -523,7 +508,6 @@ static int implicit_cell(const or_params* P, double kappa, double sigma, double 
         if (jc) {
             for (int k = 0; k < 16; k++) jc[k] = (fail || matter) ? 0.0 : Mnew[k];
             jc[16] = fail ? 0.0 : (matter ? 2.0 : 1.0);
-            for (int i = 0; i < 4; i++) jc[17 + i] = fail ? 0.0 : (X[i] - c.Xs[i]) / hdt;
         }
     }
     if (fail) {

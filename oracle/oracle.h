@@ -32,10 +32,6 @@ extern "C" {
 enum { OR_RECON_GODUNOV = 0, OR_RECON_MINMOD = 1, OR_RECON_MC = 2, OR_RECON_VANLEER = 3 };
 enum { OR_BC_OUTFLOW = 0, OR_BC_PERIODIC = 1 };
 enum { OR_IMP_NEWTON = 0, OR_IMP_PICARD = 1, OR_IMP_MATTER = 2 };
-
-/* Planes of the per-cell cache of the implicit solve: M = (J - I)/h (16), a flag,
- * and the last converged correction per unit weight D = (X - X*)/h (4). */
-#define OR_JC_PLANES 21
 enum { OR_SOLVER_PVM = 0, OR_SOLVER_RADHLL = 1 };
 
 /* status codes (per call) */

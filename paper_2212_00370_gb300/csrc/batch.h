@@ -92,7 +92,7 @@ struct StageArgs {
   int fb_pass;             // the admissibility-fallback pass a fallback launch runs, 1..kFallbackPasses
                            // (0: the main path)
   unsigned int* flagged;   // [kFallbackPasses + 1]: cells flagged with value p in this stage, or null
-  double* jc;              // [kJcPlanes][ncells] per-cell cache of the implicit solve
+  double* jc;              // [17][ncells] per-cell Jacobian cache of the implicit solve
   unsigned long long* work;  // [2] chunk counters of persistent face / cell launches
   // constrained transport (2D/3D instances when ct != 0): the staggered normal
   // field per face (one value per face, the face layout) at the step start (b0),

@@ -177,7 +177,7 @@ struct DeviceBufs {
   double *kappa = nullptr, *sigma = nullptr;
   double* Fhat = nullptr;  // [12][nfaces] FP64, or [12][nfaces] FP32 in the FP32-bulk form
   uint8_t* bad = nullptr;  // admissibility-fallback flags, one per cell
-  double* jc = nullptr;    // per-cell cache of the implicit solve, [kJcPlanes][ncells]
+  double* jc = nullptr;    // per-cell Jacobian cache of the implicit solve, [17][ncells]
   // constrained transport: staggered face field sets (with U0/V0, Ua/Va, Ub/Vb), EMFs
   double *bf0 = nullptr, *bfa = nullptr, *bfb = nullptr, *emf = nullptr;
   // per instance

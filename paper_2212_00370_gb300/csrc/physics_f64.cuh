@@ -18,10 +18,6 @@ namespace rr {
 
 constexpr int NV = 12;
 
-// Planes of the per-cell cache of the implicit solve: M = (J - I)/h (16), a flag,
-// and the last converged correction per unit weight D = (X - X*)/h (4).
-constexpr int kJcPlanes = 21;
-
 enum Status : int {
   ST_OK = 0,
   ST_C2P = 1,       // con2prim found no admissible root

@@ -226,7 +226,7 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
   A(dalloc(c, &B.smax, n_inst));
   A(dalloc(c, &B.status, n_inst));
   A(dalloc(c, &B.bad, (size_t)L.ncells));
-  A(dalloc(c, &B.jc, (size_t)rr::kJcPlanes * L.ncells));
+  A(dalloc(c, &B.jc, (size_t)17 * L.ncells));
   if (s == RRMHD_OK) {
     cudaStream_t st = c->stream;
     A(cuda_check(c, cudaMemcpyAsync(B.inst, L.inst.data(), sizeof(InstDesc) * n_inst,
@@ -256,7 +256,7 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
     A(cuda_check(c, cudaMemsetAsync(B.U0, 0, sizeof(double) * N12, st), "memset"));
     A(cuda_check(c, cudaMemsetAsync(B.V0, 0, sizeof(double) * N12, st), "memset"));
     A(cuda_check(c, cudaMemsetAsync(B.bad, 0, (size_t)L.ncells, st), "memset"));
-    A(cuda_check(c, cudaMemsetAsync(B.jc, 0, sizeof(double) * rr::kJcPlanes * L.ncells, st), "memset"));
+    A(cuda_check(c, cudaMemsetAsync(B.jc, 0, sizeof(double) * 17 * L.ncells, st), "memset"));
     A(cuda_check(c, cudaStreamSynchronize(st), "sync"));  // host vectors go out of scope
   }
   if (s == RRMHD_OK) {
@@ -630,7 +630,7 @@ rrmhd_status rrmhd_set_tuning(rrmhd_ctx* c, const rrmhd_tuning* t) {
 rrmhd_status rrmhd_autotune(rrmhd_ctx* c, int repeats, rrmhd_tuning* best, double* best_ms) {
   if (!c || repeats < 1) return set_err(c, RRMHD_EINVAL, "bad argument");
   const int n = c->L.n_inst;
-  const size_t N12 = (size_t)12 * c->L.ncells, NJ = (size_t)rr::kJcPlanes * c->L.ncells;
+  const size_t N12 = (size_t)12 * c->L.ncells, NJ = (size_t)17 * c->L.ncells;
   double *sU = nullptr, *sV = nullptr, *sJ = nullptr, *sT = nullptr, *sDt = nullptr;
   unsigned long long* sM = nullptr;
   int* sS = nullptr;

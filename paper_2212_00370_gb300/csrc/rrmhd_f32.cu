@@ -129,12 +129,12 @@ __device__ __forceinline__ int cell_update_f32(const StageArgs& a, int64_t c, co
     for (int d = 0; d < I.ndim; ++d) Ust[5 + d] = 0.5 * (a.bout[fl[d]] + a.bout[fr[d]]);
   double vs[NV];
   load12(a.Vs, N, c, vs);
-  double jc[kJcPlanes];
+  double jc[17];
 #pragma unroll
-  for (int k = 0; k < kJcPlanes; ++k) jc[k] = a.jc[k * N + c];
+  for (int k = 0; k < 17; ++k) jc[k] = a.jc[k * N + c];
   const int rc = implicit_cell(a.P, a.kappa[c], a.sigma[c], cw * dt, Ust, prim_Z(a.P, vs), Un, Vn, jc);
 #pragma unroll
-  for (int k = 0; k < kJcPlanes; ++k) a.jc[k * N + c] = jc[k];
+  for (int k = 0; k < 17; ++k) a.jc[k * N + c] = jc[k];
   return rc;
 }
 

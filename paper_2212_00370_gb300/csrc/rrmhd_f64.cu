@@ -193,12 +193,12 @@ __device__ __forceinline__ int cell_update(const StageArgs& a, int64_t c, const 
   double vs[NV];
   load12(a.Vs, N, c, vs);
   const double Zg = prim_Z(a.P, vs);
-  double jc[kJcPlanes];
+  double jc[17];
 #pragma unroll
-  for (int k = 0; k < kJcPlanes; ++k) jc[k] = a.jc[k * N + c];
+  for (int k = 0; k < 17; ++k) jc[k] = a.jc[k * N + c];
   const int rc = implicit_cell(a.P, a.kappa[c], a.sigma[c], hdt, Ust, Zg, Un, Vn, jc);
 #pragma unroll
-  for (int k = 0; k < kJcPlanes; ++k) a.jc[k * N + c] = jc[k];
+  for (int k = 0; k < 17; ++k) a.jc[k * N + c] = jc[k];
   return rc;
 }
 

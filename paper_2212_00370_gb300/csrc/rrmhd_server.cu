@@ -43,8 +43,8 @@ using rr::InstDesc;
 using rr::Params;
 
 // Bytes the server holds per resident cell: six 12-plane state buffers, two
-// copies of kappa, sigma and the cache of the implicit solve, one fallback flag.
-constexpr int64_t kBytesPerCell = 6 * 12 * 8 + 2 * (1 + 1 + rr::kJcPlanes) * 8 + 1;
+// copies of kappa, sigma and the 17-plane Jacobian cache, one fallback flag.
+constexpr int64_t kBytesPerCell = 6 * 12 * 8 + 2 * (1 + 1 + 17) * 8 + 1;
 // Per unit of face capacity: the 12-plane flux buffer; with constrained
 // transport also the three staggered face-field sets and two edge EMFs (a
 // request takes max(faces, edges / 2) units, so the edges fit in twice the
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) k_admit(Params P, const double* __re
   rr::prim2con(P, v, u);
 #pragma unroll
   for (int k = 0; k < rr::NV; ++k) U[k * n + c] = u[k];
-  for (int k = 0; k < rr::kJcPlanes; ++k) jc[k * n + c] = 0.0;
+  for (int k = 0; k < 17; ++k) jc[k * n + c] = 0.0;
 }
 
 // ---- host side -----------------------------------------------------------
@@ -285,7 +285,7 @@ bool relayout(rrmhd_server* s, int n_surv) {
     a.g[1] = {Vcur, Vnew, 12};
     a.g[2] = {s->kap[ko], s->kap[kn], 1};
     a.g[3] = {s->sig[ko], s->sig[kn], 1};
-    a.g[4] = {s->jcb[ko], s->jcb[kn], rr::kJcPlanes};
+    a.g[4] = {s->jcb[ko], s->jcb[kn], 17};
     k_gather<<<grid_for(L.cell_off[n_surv], kThreads), kThreads, 0, st>>>(a);
     SRV_CUDA(s, cudaGetLastError());
     if (ct) {
@@ -605,7 +605,7 @@ rrmhd_status rrmhd_server_create(const rrmhd_opts* opts, const rrmhd_server_conf
   for (int k = 0; k < 2; ++k) {
     A((void**)&s->kap[k], sizeof(double) * C);
     A((void**)&s->sig[k], sizeof(double) * C);
-    A((void**)&s->jcb[k], sizeof(double) * rr::kJcPlanes * C);
+    A((void**)&s->jcb[k], sizeof(double) * 17 * C);
   }
   A((void**)&B.Fhat, sizeof(double) * 12 * F);
   A((void**)&B.bad, (size_t)C);

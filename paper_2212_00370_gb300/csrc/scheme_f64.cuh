@@ -597,11 +597,9 @@ __device__ __forceinline__ bool solve_matter(const Params& P, const ImpCell& c, 
 }
 
 // Implicit step of one cell (Sec. 3.3).  Writes U and V on success; returns a Status.
-// jc (may be null): the cell's cache, kJcPlanes entries: M = (J - I)/h of its last
-// converged solve (16), a flag jc[16] and D = (X - X*)/h (4); with flag 1 the solve
-// starts from the predictor X* + h D with M (no residual at X* is needed; a start
-// that does not converge falls back to X*), M replaces C^(m) as the first matrix,
-// and the converged matrix is stored back (cleared on failure).  Flag 2: the
+// jc (may be null): the cell's Jacobian cache, M = (J - I)/h of its last converged
+// solve (16 entries) and a flag jc[16]; with flag 1 M replaces C^(m) as the first
+// matrix, and the converged matrix is stored back (cleared on failure).  Flag 2: the
 // last solve needed the matter primitives, and the next one starts there.  Order:
 // [flag 2: matter solve]; iteration on X; continuation in h on X; matter solve
 // (unless it was the first attempt).
@@ -628,19 +626,6 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
   for (int i = 0; i < 4; ++i) c.Xs[i] = Us[8 + i];
   double X[4] = {c.Xs[0], c.Xs[1], c.Xs[2], c.Xs[3]};
   double R[4], Z = Zguess;
-  if (jc && jc[16] == 1.0) {  // predictor from the cell's last converged correction
-    double Xp[4], Mp[16], Zp = Zguess;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) Xp[i] = c.Xs[i] + hdt * jc[17 + i];
-    if (imp_residual(P, c, Xp, Zguess, R, V, &Zp) && imp_newton(P, c, Xp, R, V, &Zp, jc, Mp)) {
-#pragma unroll
-      for (int k = 0; k < 16; ++k) jc[k] = Mp[k];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) jc[17 + i] = (Xp[i] - c.Xs[i]) / hdt;
-      matter_state(c, Xp, U);
-      return ST_OK;
-    }
-  }
   // no admissible matter state at X*: the explicit update U* itself is inadmissible
   if (!imp_residual(P, c, X, Zguess, R, V, &Z)) return ST_C2P;
   double Mnew[16], Vs[NV];
@@ -681,8 +666,6 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
 #pragma unroll
     for (int k = 0; k < 16; ++k) jc[k] = (ok && !matter) ? Mnew[k] : 0.0;
     jc[16] = ok ? (matter ? 2.0 : 1.0) : 0.0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) jc[17 + i] = ok ? (X[i] - c.Xs[i]) / hdt : 0.0;
   }
   if (!ok) return ST_IMPLICIT;
   matter_state(c, X, U);

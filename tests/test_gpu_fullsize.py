@@ -58,7 +58,7 @@ def oracle_cell(w, center, dt, P):
     pg = O.Grid(nd, (2 * HALF + 1,) * nd, tuple(g["dx"][:nd]), ("outflow",) * nd)
     V = np.ascontiguousarray(w.V[:, flat])
     U = O.prim2con(V, P)
-    jc = np.zeros(21 * len(flat))   # the implicit solve's per-cell cache starts empty, as on the GPU
+    jc = np.zeros(17 * len(flat))   # the implicit solve's per-cell cache starts empty, as on the GPU
     nfail = O.step(pg, dt, U, V, w.kappa[flat], w.sigma[flat], P, jcache=jc)
     m = len(flat) // 2
     return U[:, m].copy(), V[:, m].copy(), nfail

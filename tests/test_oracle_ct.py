@@ -96,7 +96,7 @@ def test_divergence_stays_at_round_off(shape, steps):
     h = min(1.0 / n for n in shape)
     div0 = np.abs(O.ct_div(g, b)).max() * h / bmax
     assert div0 < 1e-13
-    jc = np.zeros(21 * g.ncells)
+    jc = np.zeros(17 * g.ncells)
     for _ in range(steps):
         dt = O.grid_dt(g, V, P)
         assert O.step(g, dt, U, V, kappa, sigma, P, jcache=jc, bface=b) == 0
@@ -176,7 +176,7 @@ def _planar(nx, ntrans, ndim, axis, solver, steps=4):
     kN, sN = k1[idx], s1[idx]
     b = O.ct_faces_from_cells(gN, VN)
     UN = O.prim2con(VN, P)
-    jc1, jcN = np.zeros(21 * nx), np.zeros(21 * N)
+    jc1, jcN = np.zeros(17 * nx), np.zeros(17 * N)
     for _ in range(steps):
         dt = O.grid_dt(g1, Vr, P)
         assert O.step(g1, dt, U1, Vr, k1, s1, P, jcache=jc1) == 0
