@@ -39,15 +39,15 @@ sys.path.insert(0, ROOT)
 # FP64-pipe instructions (DADD + DMUL + DFMA, thread level, ncu
 # sm__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum) per cell of one launch
 # of each kernel in the steady state of this workload, averaged over the three stages
-# of the 4th step (the implicit solve's predictor makes stages 2 and 3 cheaper), measured
+# of the 4th step (their implicit weights differ, and so does the solve's work), measured
 # with ncu on a 2048-instance sample of the same distribution.
-FP64_INST_PER_ZONE = {"fp64": {"faces": 4832.0, "cells": 3986.0},
-                      "fp32_bulk": {"faces": 4.0, "cells": 3248.0},
-                      "fp64_tangent": {"faces": 5238.0, "cells": 3985.0}}
+FP64_INST_PER_ZONE = {"fp64": {"faces": 4832.0, "cells": 4237.0},
+                      "fp32_bulk": {"faces": 4.0, "cells": 3442.0},
+                      "fp64_tangent": {"faces": 5238.0, "cells": 4244.0}}
 # DRAM bytes per cell of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
-TRAFFIC_PER_CELL = {"fp64": {"faces": 240.0, "cells": 1395.0},
-                    "fp32_bulk": {"faces": 171.0, "cells": 1343.0},
-                    "fp64_tangent": {"faces": 232.0, "cells": 1395.0}}
+TRAFFIC_PER_CELL = {"fp64": {"faces": 250.0, "cells": 1303.0},
+                    "fp32_bulk": {"faces": 176.0, "cells": 1277.0},
+                    "fp64_tangent": {"faces": 241.0, "cells": 1302.0}}
 # Nominal FP64 rate of GB300: 1.25 TFLOP/s = 6.25e11 FP64-pipe instructions/s
 # (2 per SM per clock on 152 SMs at 2.07 GHz); no MEASURED_PEAKS entry exists for FP64.
 FP64_PEAK_INST = 6.25e11
