@@ -107,7 +107,6 @@ static int imp_residual_m(imp_ctx* c, const double Y[4], double R[4], double X[4
 /* Gaussian elimination with partial pivoting; A and b are overwritten. */
 int or_solve4(double A[4][4], double b[4], double x[4])
 {
-    double inv[4];   /* reciprocals of the pivots: one division per pivot */
     for (int col = 0; col < 4; col++) {
         int piv = col;
         for (int r = col + 1; r < 4; r++)
@@ -123,9 +122,8 @@ int or_solve4(double A[4][4], double b[4], double x[4])
             b[col] = b[piv];
             b[piv] = t;
         }
-        inv[col] = 1.0 / A[col][col];
         for (int r = col + 1; r < 4; r++) {
-            double f = A[r][col] * inv[col];
+            double f = A[r][col] / A[col][col];
             for (int k = col + 1; k < 4; k++) A[r][k] = A[r][k] - f * A[col][k];
             b[r] = b[r] - f * b[col];
         }
@@ -133,7 +131,7 @@ int or_solve4(double A[4][4], double b[4], double x[4])
     for (int r = 3; r >= 0; r--) {
         double s = b[r];
         for (int k = r + 1; k < 4; k++) s = s - A[r][k] * x[k];
-        x[r] = s * inv[r];
+        x[r] = s / A[r][r];
     }
     return 0;
 }
@@ -325,10 +323,9 @@ static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z,
             double dR[4];
             for (int i = 0; i < 4; i++) dR[i] = Rn[i] - R[i];
             double s2 = ((dX[0] * dX[0] + dX[1] * dX[1]) + dX[2] * dX[2]) + dX[3] * dX[3];
-            double is2 = 1.0 / s2;
             for (int i = 0; i < 4; i++) {
                 double Jd = ((J[i][0] * dX[0] + J[i][1] * dX[1]) + J[i][2] * dX[2]) + J[i][3] * dX[3];
-                double q = (dR[i] - Jd) * is2;
+                double q = (dR[i] - Jd) / s2;
                 for (int j = 0; j < 4; j++) J[i][j] = J[i][j] + q * dX[j];
             }
             fresh_fd = 0;

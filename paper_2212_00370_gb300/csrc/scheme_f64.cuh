@@ -265,7 +265,6 @@ static __device__ __noinline__ bool imp_residual(const Params& P, const ImpCell&
 
 // Gaussian elimination with partial pivoting (A, b overwritten); false if singular.
 __device__ __forceinline__ bool solve4(double A[4][4], double b[4], double x[4]) {
-  double inv[4];  // reciprocals of the pivots: one division per pivot
 #pragma unroll
   for (int col = 0; col < 4; ++col) {
     int piv = col;
@@ -284,10 +283,9 @@ __device__ __forceinline__ bool solve4(double A[4][4], double b[4], double x[4])
       b[col] = b[piv];
       b[piv] = t;
     }
-    inv[col] = 1.0 / A[col][col];
 #pragma unroll
     for (int r = col + 1; r < 4; ++r) {
-      const double f = A[r][col] * inv[col];
+      const double f = A[r][col] / A[col][col];
 #pragma unroll
       for (int k = col + 1; k < 4; ++k) A[r][k] = A[r][k] - f * A[col][k];
       b[r] = b[r] - f * b[col];
@@ -298,7 +296,7 @@ __device__ __forceinline__ bool solve4(double A[4][4], double b[4], double x[4])
     double s = b[r];
 #pragma unroll
     for (int k = r + 1; k < 4; ++k) s = s - A[r][k] * x[k];
-    x[r] = s * inv[r];
+    x[r] = s / A[r][r];
   }
   return true;
 }
@@ -443,12 +441,11 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
     }
     {  // Broyden: J += (dR - J dX) dX^T / (dX . dX)
       const double s2 = ((dX[0] * dX[0] + dX[1] * dX[1]) + dX[2] * dX[2]) + dX[3] * dX[3];
-      const double is2 = 1.0 / s2;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const double dRi = Rn[i] - R[i];
         const double Jd = ((J[i][0] * dX[0] + J[i][1] * dX[1]) + J[i][2] * dX[2]) + J[i][3] * dX[3];
-        const double q = (dRi - Jd) * is2;
+        const double q = (dRi - Jd) / s2;
 #pragma unroll
         for (int j = 0; j < 4; ++j) J[i][j] = J[i][j] + q * dX[j];
       }
