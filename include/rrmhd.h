@@ -161,8 +161,12 @@ rrmhd_status rrmhd_get_inst_status(const rrmhd_ctx* ctx, int32_t* status);
  * step takes dt = cfl / max sum_d lambda_d/dx_d (clipped to t_end) and runs
  * three stages of {PLM + PVM-int-8 flux at every face (Sec. 3.2), flux
  * difference and RK combination (Eq. explicit), implicit radiation-matter solve
- * (Sec. 3.3)} with implicit weights 1, 1/4, 2/3.  Enqueued as one CUDA graph
- * per step; returns without synchronising. */
+ * (Sec. 3.3)} with implicit weights 1, 1/4, 2/3.  A cell whose update has no
+ * admissible state (no con2prim root, or no converged implicit solve) gets the
+ * first-order Rusanov flux at its faces and is updated again with its neighbours,
+ * in up to three passes (a neighbour that then fails is flagged in turn); only a
+ * failure after that freezes the instance.  Enqueued as one CUDA graph per step;
+ * returns without synchronising. */
 rrmhd_status rrmhd_imex_step(rrmhd_ctx* ctx, int nsteps);
 
 /* Same as rrmhd_imex_step, from and to HOST buffers: copies V_in (host
