@@ -247,3 +247,34 @@ def test_failed_request_does_not_disturb_the_others():
         j = ids[res["id"]]
         assert res["status"] == alone[j][0]["status"]
         compare_bitwise(out, alone[j][1], f"request {j}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_server_ct_3d_request_in_a_mix(precision):
+    """A 3D request (6x5x4, periodic) under constrained transport: its edges outnumber
+    its faces, so it takes max(faces, edges/2) units of face capacity.  It shares the
+    device with 1D requests that arrive after it (each arrival repacks the batch and
+    moves its face field), and its result equals the context path's bit for bit."""
+    from test_gpu_ct import instance
+    g, V, b, k, s = instance((6, 5, 4), 8)
+    te = 0.05
+    Vc, tc, stc = run_context((g, V, k, s, te), precision, ct=1)
+    assert stc == 0
+    others = [r for r in small_requests(10, seed=29) if r[0]["ndim"] == 1][:4]
+    srv = rrmhd.Server(gamma=GAMMA, precision=precision, lanes=2, mem_bytes=1 << 28, ct=1)
+    ids = {srv.submit(grid_of(others[0][0]), *others[0][1:]): "1d"}
+    time.sleep(0.02)
+    ids[srv.submit(grid_of(g), V, k, s, te)] = "3d"
+    for r in others[1:]:
+        time.sleep(0.01)
+        ids[srv.submit(grid_of(r[0]), *r[1:])] = "1d"
+    srv.wait_idle(300)
+    got = srv.poll()
+    st = srv.stats()
+    srv.close()
+    assert len(got) == len(others) + 1 and st["relayouts"] >= 2
+    res3 = [(res, out) for res, out in got if ids[res["id"]] == "3d"]
+    assert len(res3) == 1
+    res, out = res3[0]
+    assert res["status"] == 0 and res["t"] == tc
+    compare_bitwise(out, Vc, "3D request in the mix vs context (constrained transport)")
