@@ -7,7 +7,9 @@
   * the implicit solve in the matter primitives, on radiation-dominated cells
     where the iteration on X fails (through rrmhd_implicit_source), and over
     many steps of the 2D blast (128^2, constrained transport), where it, the
-    fallback passes and the per-cell record of the form used all take part.
+    fallback passes and the per-cell record of the form used all take part;
+  * the fallback under constrained transport next to outflow boundaries (its
+    Rusanov fluxes in the edge EMFs, the 3x3 block updated again).
 """
 import numpy as np
 import pytest
@@ -101,3 +103,34 @@ def test_blast_2d_many_steps_bitwise():
     compare_bitwise(Vg, V, "blast V")
     compare_bitwise(ctx.get_face_field().cpu().numpy(), b, "blast face field")
     assert ctx.get_times()[0][0] == t
+
+
+def test_ct_fallback_outflow_strip_bitwise():
+    """A planar 2D serving request (C1 states, outflow on every side) cut to a
+    415 x 4 strip, with constrained transport, 60 steps: the fallback fires next
+    to the outflow boundaries, its Rusanov fluxes enter the edge EMFs, and the
+    3x3 block around each flagged cell is updated again.  Bit for bit."""
+    spec = W.serving_requests(32, rate=200.0)[12]
+    g0, V0, k0, s0, _ = W.serving_request(spec)
+    n, ny = g0["n"][0], 4
+    g = {"ndim": 2, "n": (n, ny, 1), "dx": (1.0 / n, 1.0 / n, 1.0), "bc": ("outflow",) * 3}
+    V = np.ascontiguousarray(V0[:, :n * ny]).copy()
+    k, s = k0[:n * ny].copy(), s0[:n * ny].copy()
+    w = W.Workload("strip", [g], V, k, s, np.array([np.inf]), 4.0 / 3.0)
+    P = oracle_params(w)
+    og = oracle_grid(g)
+    Vo = V.copy()
+    b = O.ct_faces_from_cells(og, Vo)
+    O.ct_canonical(og, b)
+    O.ct_cells_from_faces(og, b, np.zeros_like(Vo), Vo)
+    U = O.prim2con(Vo, P)
+    st_o = O.Stats()
+    t, steps, nfail = O.run(og, 0.0, np.inf, U, Vo, k, s, P, max_steps=60, stats=st_o, bface=b)
+    assert nfail == 0 and steps == 60 and st_o.fallback_cells > 0
+    ctx = gpu_context(w, ct=1)
+    ctx.imex_step(60)
+    Ug, Vg = (x.cpu().numpy() for x in ctx.get_state())
+    assert ctx.inst_status()[0] == 0
+    compare_bitwise(Ug, U, "strip U")
+    compare_bitwise(Vg, Vo, "strip V")
+    compare_bitwise(ctx.get_face_field().cpu().numpy(), b, "strip face field")
