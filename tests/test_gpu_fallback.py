@@ -9,7 +9,8 @@
     many steps of the 2D blast (128^2, constrained transport), where it, the
     fallback passes and the per-cell record of the form used all take part;
   * the fallback under constrained transport next to outflow boundaries (its
-    Rusanov fluxes in the edge EMFs, the 3x3 block updated again).
+    Rusanov fluxes in the edge EMFs, the 3x3 block updated again), and in a 3D
+    periodic blast (3x3x3 blocks).
 """
 import numpy as np
 import pytest
@@ -134,3 +135,31 @@ def test_ct_fallback_outflow_strip_bitwise():
     compare_bitwise(Ug, U, "strip U")
     compare_bitwise(Vg, Vo, "strip V")
     compare_bitwise(ctx.get_face_field().cpu().numpy(), b, "strip face field")
+
+
+def test_ct_fallback_3d_blast_bitwise():
+    """A 12^3 periodic blast with constrained transport, 20 steps: the fallback fires
+    in 3D (all three EMF components recomputed, 3x3x3 blocks updated again) and the
+    matter-primitive solve takes part.  State and face field bit for bit."""
+    from test_oracle_ct import blast_3d
+    n = 12
+    V, k, s = blast_3d(n)
+    g = {"ndim": 3, "n": (n, n, n), "dx": (1.0 / n,) * 3, "bc": ("periodic",) * 3}
+    w = W.Workload("blast-3d", [g], np.ascontiguousarray(V), k, s, np.array([np.inf]), 4.0 / 3.0)
+    P = oracle_params(w)
+    og = oracle_grid(g)
+    Vo = V.copy()
+    b = O.ct_faces_from_cells(og, Vo)
+    O.ct_canonical(og, b)
+    O.ct_cells_from_faces(og, b, np.zeros_like(Vo), Vo)
+    U = O.prim2con(Vo, P)
+    st_o = O.Stats()
+    t, steps, nfail = O.run(og, 0.0, np.inf, U, Vo, k, s, P, max_steps=20, stats=st_o, bface=b)
+    assert nfail == 0 and steps == 20 and st_o.fallback_cells > 0 and st_o.imp_matter > 0
+    ctx = gpu_context(w, ct=1)
+    ctx.imex_step(20)
+    Ug, Vg = (x.cpu().numpy() for x in ctx.get_state())
+    assert ctx.inst_status()[0] == 0
+    compare_bitwise(Ug, U, "3D blast U")
+    compare_bitwise(Vg, Vo, "3D blast V")
+    compare_bitwise(ctx.get_face_field().cpu().numpy(), b, "3D blast face field")
