@@ -42,7 +42,7 @@ class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "c2p_calls", "c2p_iters", "c2p_fail", "flux_evals", "pvm_faces", "pvm_fallback",
         "imp_cells", "imp_iters", "imp_resid", "imp_jac", "imp_fail", "imp_matter", "imp_resid_max",
-        "fallback_cells", "fallback_flagged")]
+        "fallback_cells", "fallback_flagged", "imp_polish")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -114,6 +114,7 @@ def lib():
             "or_signal_speed_n": (None, [P, C.c_int, i64, dp, dp]),
             "or_pvm_flux_n": (None, [P, C.c_int, i64, dp, dp, dp, dp, dp, dp, i32p, S]),
             "or_implicit_n": (None, [P, i64, dp, dp, C.c_double, dp, dp, dp, dp, i32p, S]),
+            "or_implicit_cn": (None, [P, i64, dp, dp, C.c_double, dp, dp, dp, dp, dp, i32p, S]),
             "or_four_force": (None, [C.c_double, C.c_double, C.c_double, dp, C.c_double,
                                      C.c_double, C.c_double, dp, dp, dp]),
             "or_m1_pressure": (None, [C.c_double, dp, dp]),
@@ -248,6 +249,23 @@ def implicit(Ustar, kappa, sigma, hdt, P, Zguess=None, stats=None):
                         _d(zg) if zg is not None else None, _d(U), _d(V), _i32(st), _stats(stats))
     if sq:
         return U[:, 0], V[:, 0], int(st[0])
+    return U, V, st
+
+
+def implicit_cached(Ustar, kappa, sigma, hdt, P, jcache, Zguess=None, stats=None):
+    """The implicit step of n cells with their Jacobian cache jcache ((17, n) float64,
+    zero = empty; updated in place, as a grid step does).  Returns (U, V, status)."""
+    Us, n, _ = _soa(Ustar)
+    assert jcache.shape == (17, n) and jcache.dtype == np.float64 and jcache.flags.c_contiguous
+    k = np.ascontiguousarray(np.broadcast_to(kappa, (n,)), dtype=np.float64)
+    s = np.ascontiguousarray(np.broadcast_to(sigma, (n,)), dtype=np.float64)
+    zg = None if Zguess is None else np.ascontiguousarray(np.broadcast_to(Zguess, (n,)), dtype=np.float64)
+    U = np.zeros_like(Us)
+    V = np.zeros_like(Us)
+    st = np.zeros(n, dtype=np.int32)
+    lib().or_implicit_cn(C.byref(P.struct()), n, _d(k), _d(s), float(hdt), _d(Us),
+                         _d(zg) if zg is not None else None, _d(U), _d(V), _d(jcache), _i32(st),
+                         _stats(stats))
     return U, V, st
 
 

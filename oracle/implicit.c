@@ -216,6 +216,75 @@ static void picard_jacobian(const imp_ctx* c, const double X[4], const double V[
     or_picard_matrix(c->kappa, c->sigma, c->hdt, V[0], u, W, 0.0, Dr, c->Xs, J, rhs);
 }
 
+/* Forward-difference Jacobian of R at X (step 1e-7 E_r; a backward step where
+ * the forward one leaves the admissible set).  Returns 1 if neither is admissible. */
+static int fd_jacobian(imp_ctx* c, const double X[4], const double R[4], double Z, double J[4][4])
+{
+    double h = 1e-7 * X[0];
+    for (int j = 0; j < 4; j++) {
+        double Xp[4] = {X[0], X[1], X[2], X[3]};
+        double Rp[4], Vp[12], Zp;
+        Xp[j] = X[j] + h;
+        if (imp_residual(c, Xp, Z, Rp, Vp, &Zp)) {
+            Xp[j] = X[j] - h;
+            if (imp_residual(c, Xp, Z, Rp, Vp, &Zp)) return 1;
+        }
+        double dXj = Xp[j] - X[j];
+        for (int i = 0; i < 4; i++) J[i][j] = (Rp[i] - R[i]) / dXj;
+    }
+    return 0;
+}
+
+#define IMP_POLISH_TOL 1e-14  /* polished root: last correction <= 1e-14 E_r */
+#define IMP_POLISH_MAX 6      /* at most six polishing corrections           */
+
+/* Polish of a converged iterate.  Convergence at imp_tol leaves an error of about
+ * the last step times the matrix's contraction, and that contraction depends on
+ * how the iterate was reached (the first matrix, the Broyden history, the cell's
+ * cache): left there, the result would be a function of the solver's path rather
+ * than of the state.  It is refined here towards the root of R itself: corrections
+ * dX = -J^-1 R(X), each accepted without line search, J updated by Broyden's
+ * formula after each, until a correction is <= 1e-14 E_r.  A correction that does
+ * not halve the previous one means the rounding floor of R is reached: the polish
+ * stops there without taking it.  last is the size of the converged step.  X, R,
+ * V and Z are updated in place and stay those of the last accepted iterate. */
+static void polish(imp_ctx* c, double J[4][4], double X[4], double R[4], double V[12], double* Z,
+                   double last)
+{
+    double prev = last;
+    for (int p = 0; p < IMP_POLISH_MAX; p++) {
+        double A[4][4], b[4], dX[4];
+        for (int i = 0; i < 4; i++) {
+            b[i] = -R[i];
+            for (int j = 0; j < 4; j++) A[i][j] = J[i][j];
+        }
+        if (or_solve4(A, b, dX)) return;
+        double d = 0.0;
+        for (int i = 0; i < 4; i++) d = fabs(dX[i]) > d ? fabs(dX[i]) : d;
+        if (d <= IMP_POLISH_TOL * X[0]) return;
+        if (p > 0 && d > 0.5 * prev) return;
+        double Xn[4], Rn[4], Vn[12], Zn = *Z;
+        for (int i = 0; i < 4; i++) Xn[i] = X[i] + dX[i];
+        if (imp_residual(c, Xn, *Z, Rn, Vn, &Zn)) return;
+        if (c->st) c->st->imp_polish++;
+        {
+            double s2 = ((dX[0] * dX[0] + dX[1] * dX[1]) + dX[2] * dX[2]) + dX[3] * dX[3];
+            for (int i = 0; i < 4; i++) {
+                double Jd = ((J[i][0] * dX[0] + J[i][1] * dX[1]) + J[i][2] * dX[2]) + J[i][3] * dX[3];
+                double q = ((Rn[i] - R[i]) - Jd) / s2;
+                for (int j = 0; j < 4; j++) J[i][j] = J[i][j] + q * dX[j];
+            }
+        }
+        for (int i = 0; i < 4; i++) {
+            X[i] = Xn[i];
+            R[i] = Rn[i];
+        }
+        for (int k = 0; k < 12; k++) V[k] = Vn[k];
+        *Z = Zn;
+        prev = d;
+    }
+}
+
 /* Quasi-Newton iteration on R(X) = 0.
  * The first matrix is the paper's C^(m) (the Jacobian with matter and Eddington
  * tensor frozen), so the first iterate is the iteration of Sec. 3.3.  Each
@@ -244,18 +313,7 @@ static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z,
     }
     for (int m = 1; m <= P->imp_maxit; m++) {
         if (need_fd) {
-            double h = 1e-7 * X[0];
-            for (int j = 0; j < 4; j++) {
-                double Xp[4] = {X[0], X[1], X[2], X[3]};
-                double Rp[4], Vp[12], Zp;
-                Xp[j] = X[j] + h;
-                if (imp_residual(c, Xp, *Z, Rp, Vp, &Zp)) {
-                    Xp[j] = X[j] - h;
-                    if (imp_residual(c, Xp, *Z, Rp, Vp, &Zp)) return 1;
-                }
-                double dXj = Xp[j] - X[j];
-                for (int i = 0; i < 4; i++) J[i][j] = (Rp[i] - R[i]) / dXj;
-            }
+            if (fd_jacobian(c, X, R, *Z, J)) return 1;
             need_fd = 0;
             fresh_fd = 1;
             first = 0;
@@ -289,6 +347,7 @@ static int newton(imp_ctx* c, double X[4], double R[4], double V[12], double* Z,
                 for (int i = 0; i < 4; i++)
                     for (int j = 0; j < 4; j++)
                         Mout[4 * i + j] = (J[i][j] - (i == j ? 1.0 : 0.0)) / c->hdt;
+            polish(c, J, X, R, V, Z, dfull);
             return 0;
         }
         /* backtracking line search: halve the step, at most ten times, until the
@@ -542,6 +601,25 @@ void or_implicit_n(const or_params* P, int64_t n, const double* kappa, const dou
         double us[12], u[12] = {0}, v[12] = {0};
         for (int k = 0; k < 12; k++) us[k] = Ustar[k * n + i];
         status[i] = or_implicit(P, kappa[i], sigma[i], hdt, us, Zg ? Zg[i] : 0.0, u, v, st);
+        for (int k = 0; k < 12; k++) {
+            U[k * n + i] = u[k];
+            V[k * n + i] = v[k];
+        }
+    }
+}
+
+/* or_implicit_n with a per-cell Jacobian cache jcache ([17][n] planes, zero =
+ * empty), read and written back as or_implicit_c does for one cell. */
+void or_implicit_cn(const or_params* P, int64_t n, const double* kappa, const double* sigma,
+                    double hdt, const double* Ustar, const double* Zg, double* U, double* V,
+                    double* jcache, int32_t* status, or_stats* st)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double us[12], u[12] = {0}, v[12] = {0}, jc[17];
+        for (int k = 0; k < 12; k++) us[k] = Ustar[k * n + i];
+        for (int k = 0; k < 17; k++) jc[k] = jcache[k * n + i];
+        status[i] = or_implicit_c(P, kappa[i], sigma[i], hdt, us, Zg ? Zg[i] : 0.0, u, v, jc, st);
+        for (int k = 0; k < 17; k++) jcache[k * n + i] = jc[k];
         for (int k = 0; k < 12; k++) {
             U[k * n + i] = u[k];
             V[k * n + i] = v[k];

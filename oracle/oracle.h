@@ -70,6 +70,7 @@ typedef struct {
     int64_t imp_resid_max;     /* most residual evaluations of one cell's solve */
     int64_t fallback_cells;    /* cell updates repeated by the admissibility fallback */
     int64_t fallback_flagged;  /* cells flagged by it after its first pass */
+    int64_t imp_polish;        /* polishing corrections of converged implicit solves */
 } or_stats;
 
 void or_params_init(or_params* P);
@@ -178,6 +179,9 @@ void or_pvm_flux_n(const or_params* P, int dir, int64_t n, const double* VL, con
 void or_implicit_n(const or_params* P, int64_t n, const double* kappa, const double* sigma,
                    double hdt, const double* Ustar, const double* Zg, double* U, double* V,
                    int32_t* status, or_stats* st);
+void or_implicit_cn(const or_params* P, int64_t n, const double* kappa, const double* sigma,
+                    double hdt, const double* Ustar, const double* Zg, double* U, double* V,
+                    double* jcache, int32_t* status, or_stats* st);
 
 #ifdef __cplusplus
 }
