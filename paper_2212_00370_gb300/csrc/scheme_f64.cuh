@@ -333,12 +333,89 @@ __device__ __forceinline__ void picard_matrix(const ImpCell& c, const double* X,
   }
 }
 
+// Forward-difference Jacobian of R at X (step 1e-7 E_r; a backward step where the
+// forward one leaves the admissible set).  False if neither is admissible.
+static __device__ __noinline__ bool fd_jacobian(const Params& P, const ImpCell& c, const double* X,
+                                                const double* R, double Z, double J[4][4]) {
+  const double h = 1e-7 * X[0];
+  for (int j = 0; j < 4; ++j) {
+    double Xp[4] = {X[0], X[1], X[2], X[3]};
+    double Rp[4], Vp[NV], Zp;
+    Xp[j] = X[j] + h;
+    if (!imp_residual(P, c, Xp, Z, Rp, Vp, &Zp)) {
+      Xp[j] = X[j] - h;
+      if (!imp_residual(P, c, Xp, Z, Rp, Vp, &Zp)) return false;
+    }
+    const double dXj = Xp[j] - X[j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) J[i][j] = (Rp[i] - R[i]) / dXj;
+  }
+  return true;
+}
+
+constexpr double IMP_POLISH_TOL = 1e-14;  // polished root: last correction <= 1e-14 E_r
+constexpr int IMP_POLISH_MAX = 6;         // at most six polishing corrections
+
+// Polish of a converged iterate.  Stopping at imp_tol leaves an error of about the
+// last step times the matrix's contraction, which depends on how the iterate was
+// reached (first matrix, Broyden history, the cell's cache).  The iterate is refined
+// towards the root of R itself, so that the result is a function of the cell's state:
+// corrections dX = -J^-1 R(X), accepted without line search, J updated by Broyden's
+// formula after each, until a correction is <= 1e-14 E_r.  A correction that does not
+// halve the previous one means the rounding floor of R is reached: the polish stops
+// there without taking it.  last is the size of the converged step.  X, R, V and Z
+// stay those of the last accepted iterate.
+static __device__ __noinline__ void imp_polish(const Params& P, const ImpCell& c, double J[4][4],
+                                               double* X, double* R, double* V, double* Z,
+                                               double last) {
+  double prev = last;
+  for (int p = 0; p < IMP_POLISH_MAX; ++p) {
+    double A[4][4], b[4], dX[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      b[i] = -R[i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) A[i][j] = J[i][j];
+    }
+    if (!solve4(A, b, dX)) return;
+    double d = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d = fabs(dX[i]) > d ? fabs(dX[i]) : d;
+    if (d <= IMP_POLISH_TOL * X[0]) return;
+    if (p > 0 && d > 0.5 * prev) return;
+    double Xn[4], Rn[4], Vn[NV], Zn = *Z;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Xn[i] = X[i] + dX[i];
+    if (!imp_residual(P, c, Xn, *Z, Rn, Vn, &Zn)) return;
+    {  // Broyden: J += (dR - J dX) dX^T / (dX . dX)
+      const double s2 = ((dX[0] * dX[0] + dX[1] * dX[1]) + dX[2] * dX[2]) + dX[3] * dX[3];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const double Jd = ((J[i][0] * dX[0] + J[i][1] * dX[1]) + J[i][2] * dX[2]) + J[i][3] * dX[3];
+        const double q = ((Rn[i] - R[i]) - Jd) / s2;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) J[i][j] = J[i][j] + q * dX[j];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      X[i] = Xn[i];
+      R[i] = Rn[i];
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) V[k] = Vn[k];
+    *Z = Zn;
+    prev = d;
+  }
+}
+
 // Quasi-Newton iteration on R(X) = 0: first matrix C^(m) (the paper's
 // frozen-matter iteration), Broyden rank-one update after every accepted step,
 // forward-difference Jacobian (step 1e-7 E_r) when successive steps contract by
 // less than 2x or no descent is found; Armijo backtracking on |R|^2 (at most ten
 // halvings); converged
-// when the full step is <= imp_tol * E_r.  Returns true on convergence.
+// when the full step is <= imp_tol * E_r, then polished (imp_polish).  Returns true
+// on convergence.
 static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c, double* X, double* R,
                                         double* V, double* Z, const double* Min, double* Mout) {
   double J[4][4];
@@ -354,19 +431,7 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
   }
   for (int m = 1; m <= P.imp_maxit; ++m) {
     if (need_fd) {
-      const double h = 1e-7 * X[0];
-      for (int j = 0; j < 4; ++j) {
-        double Xp[4] = {X[0], X[1], X[2], X[3]};
-        double Rp[4], Vp[NV], Zp;
-        Xp[j] = X[j] + h;
-        if (!imp_residual(P, c, Xp, *Z, Rp, Vp, &Zp)) {
-          Xp[j] = X[j] - h;
-          if (!imp_residual(P, c, Xp, *Z, Rp, Vp, &Zp)) return false;
-        }
-        const double dXj = Xp[j] - X[j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) J[i][j] = (Rp[i] - R[i]) / dXj;
-      }
+      if (!fd_jacobian(P, c, X, R, *Z, J)) return false;
       need_fd = 0;
       fresh_fd = 1;
       first = 0;
@@ -406,6 +471,7 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) Mout[4 * i + j] = (J[i][j] - (i == j ? 1.0 : 0.0)) / c.hdt;
+      imp_polish(P, c, J, X, R, V, Z, dfull);
       return true;
     }
     const double r0 = ((R[0] * R[0] + R[1] * R[1]) + R[2] * R[2]) + R[3] * R[3];
