@@ -32,6 +32,27 @@ static __device__ __forceinline__ void load12(const double* __restrict__ A, int6
   for (int k = 0; k < NV; ++k) x[k] = __ldg(A + k * stride + c);
 }
 
+// Warp-level maximum of the CFL signal-speed bits onto the instances' smax words.
+// Every lane of the warp calls it (inst = -1 for a lane with nothing to add); blocks
+// are whole warps.  Cells of an instance are contiguous, so lanes with the same inst
+// form runs: a segmented max over each run reaches its first lane, which issues the
+// run's one atomicMax.  The bits of non-negative doubles order like their values
+// (a NaN above every number), and a maximum does not depend on the order it is
+// taken in, so smax ends as with one atomicMax per cell.
+static __device__ __forceinline__ void warp_smax(unsigned long long* smax, int inst,
+                                                 unsigned long long v) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long ov = __shfl_down_sync(full, v, off);
+    const int oi = __shfl_down_sync(full, inst, off);
+    if (lane + off < 32 && oi == inst && ov > v) v = ov;
+  }
+  const int pi = __shfl_up_sync(full, inst, 1);
+  if (inst >= 0 && (lane == 0 || pi != inst)) atomicMax(smax + inst, v);
+}
+
 static __device__ __forceinline__ bool inst_active(const Batch& b, int i) {
   return b.st.status[i] == 0 && b.st.dt[i] > 0.0;
 }

@@ -41,12 +41,16 @@ __device__ __forceinline__ void persistent_items(int64_t n, unsigned long long* 
 
 // The shapes that are compiled: block size x items per thread (grid schedule) and
 // block size (persistent schedule).
-#define RR_GRID_SHAPES(X) X(32, 1) X(32, 2) X(64, 1) X(64, 2) X(128, 1) X(128, 2) X(256, 1) X(256, 2)
+// Blocks of 8 and 16 threads (grid schedule, one item per thread) spread a small
+// grid over more SMs with partial warps.
+#define RR_GRID_SHAPES(X) \
+  X(8, 1) X(16, 1) X(32, 1) X(32, 2) X(64, 1) X(64, 2) X(128, 1) X(128, 2) X(256, 1) X(256, 2)
 #define RR_PERSISTENT_BLOCKS(X) X(32) X(64) X(128) X(256)
 
 inline bool shape_ok(int block, int per_thread, int persistent) {
   const bool bs = block == 32 || block == 64 || block == 128 || block == 256;
   if (persistent) return bs && per_thread == 1 && persistent == 1;
+  if (block == 8 || block == 16) return per_thread == 1 && persistent == 0;
   return bs && (per_thread == 1 || per_thread == 2) && persistent == 0;
 }
 

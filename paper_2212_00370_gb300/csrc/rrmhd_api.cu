@@ -704,11 +704,12 @@ rrmhd_status rrmhd_autotune(rrmhd_ctx* c, int repeats, rrmhd_tuning* best, doubl
       cur_best = cand;
     }
   };
-  const int blocks[4] = {32, 64, 128, 256};
+  const int blocks[6] = {8, 16, 32, 64, 128, 256};
   // 1. cell shapes
   for (int persistent = 0; persistent <= 1; ++persistent)
     for (int bsz : blocks)
       for (int pt = 1; pt <= (persistent ? 1 : 2); ++pt) {
+        if (!rr::shape_ok(bsz, pt, persistent)) continue;
         rrmhd_tuning t = cur_best;
         t.cell_block = bsz;
         t.cell_per_thread = pt;
@@ -719,6 +720,7 @@ rrmhd_status rrmhd_autotune(rrmhd_ctx* c, int repeats, rrmhd_tuning* best, doubl
   for (int persistent = 0; persistent <= 1; ++persistent)
     for (int bsz : blocks)
       for (int pt = 1; pt <= (persistent ? 1 : 2); ++pt) {
+        if (!rr::shape_ok(bsz, pt, persistent)) continue;
         rrmhd_tuning t = cur_best;
         t.face_block = bsz;
         t.face_per_thread = pt;

@@ -3,8 +3,9 @@
 // Faces (PLM, fluxes, PVM-int-8 with tangent products, the Rusanov fallback) and
 // the flux difference run in FP32; con2prim of the cells, the implicit
 // radiation-matter solve and the accumulation of U stay in FP64 (the same solver
-// as the FP64 path, compiled here with fused multiply-add).  Same launch
-// structure and lanes as rrmhd_f64.cu.
+// as the FP64 path, compiled here with fused multiply-add; the iteration's
+// approximate matrix is kept, solved and updated in FP32, while its residual, iterate
+// and convergence tests stay FP64).  Same launch structure and lanes as rrmhd_f64.cu.
 #include <cuda_runtime.h>
 
 #include "batch.h"
@@ -132,7 +133,7 @@ __device__ __forceinline__ int cell_update_f32(const StageArgs& a, int64_t c, co
   double jc[17];
 #pragma unroll
   for (int k = 0; k < 17; ++k) jc[k] = a.jc[k * N + c];
-  const int rc = implicit_cell(a.P, a.kappa[c], a.sigma[c], cw * dt, Ust, prim_Z(a.P, vs), Un, Vn, jc);
+  const int rc = implicit_cell<float>(a.P, a.kappa[c], a.sigma[c], cw * dt, Ust, prim_Z(a.P, vs), Un, Vn, jc);
 #pragma unroll
   for (int k = 0; k < 17; ++k) a.jc[k * N + c] = jc[k];
   return rc;
@@ -212,10 +213,11 @@ __global__ void __launch_bounds__(kFaceThreads) k_fallback_faces_f32(StageArgs a
   for (int k = 0; k < NV; ++k) a.Fhat32[k * a.fstride + g] = F[k];
 }
 
-__global__ void __launch_bounds__(kCellThreads) k_fallback_cells_f32(StageArgs a) {
+// One cell of a fallback pass; in the last pass of stage 3, inst and s receive the
+// cell's instance and CFL signal speed (left at -1 where the cell adds none).
+__device__ __forceinline__ void fallback_cell_f32(const StageArgs& a, int64_t c, int& inst,
+                                                  double& s) {
   const Batch& b = a.b;
-  const int64_t c = b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= b.c_end) return;
   const CellPos q = cell_pos(b, c);
   const int pass = a.fb_pass;
   const bool last = pass == kFallbackPasses;
@@ -277,10 +279,20 @@ __global__ void __launch_bounds__(kCellThreads) k_fallback_cells_f32(StageArgs a
     load12(a.Vout, b.ncells, c, Vn);
   }
   if (a.stage == 3 && last) {
-    double s = signal_speed(a.P, 0, Vn) / I.dx[0];
+    s = signal_speed(a.P, 0, Vn) / I.dx[0];
     for (int d = 1; d < I.ndim; ++d) s = s + signal_speed(a.P, d, Vn) / I.dx[d];
-    atomicMax(b.st.smax + q.i, (unsigned long long)__double_as_longlong(s));
+    inst = q.i;
   }
+}
+
+__global__ void __launch_bounds__(kCellThreads) k_fallback_cells_f32(StageArgs a) {
+  const int64_t c = a.b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int inst = -1;
+  double s = 0.0;
+  if (c < a.b.c_end) fallback_cell_f32(a, c, inst, s);
+  // the CFL maximum of the next step (launch-uniform condition: every lane gets here)
+  if (a.stage == 3 && a.fb_pass == kFallbackPasses)
+    warp_smax(a.b.st.smax, inst, (unsigned long long)__double_as_longlong(s));
 }
 
 __global__ void k_widen(const float* __restrict__ F32, int64_t fs32, int64_t f_begin, int64_t n,

@@ -286,10 +286,10 @@ __global__ void __launch_bounds__(kFaceThreads) k_fallback_faces(StageArgs a) {
 // for the next pass; in the last pass it fails its instance.  The last pass of
 // stage 3 also reduces the next CFL signal speed of every cell and carries
 // inactive instances over.
-__global__ void __launch_bounds__(kCellThreads, RR_CELL_MIN_BLOCKS) k_fallback_cells(StageArgs a) {
+// One cell of a fallback pass; in the last pass of stage 3, inst and s receive the
+// cell's instance and CFL signal speed (left at -1 where the cell adds none).
+__device__ __forceinline__ void fallback_cell(const StageArgs& a, int64_t c, int& inst, double& s) {
   const Batch& b = a.b;
-  const int64_t c = b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= b.c_end) return;
   const CellPos q = cell_pos(b, c);
   const int pass = a.fb_pass;
   const bool last = pass == kFallbackPasses;
@@ -353,10 +353,20 @@ __global__ void __launch_bounds__(kCellThreads, RR_CELL_MIN_BLOCKS) k_fallback_c
     load12(a.Vout, b.ncells, c, Vn);
   }
   if (a.stage == 3 && last) {
-    double s = signal_speed(a.P, 0, Vn) / I.dx[0];
+    s = signal_speed(a.P, 0, Vn) / I.dx[0];
     for (int d = 1; d < I.ndim; ++d) s = s + signal_speed(a.P, d, Vn) / I.dx[d];
-    atomicMax(b.st.smax + q.i, (unsigned long long)__double_as_longlong(s));
+    inst = q.i;
   }
+}
+
+__global__ void __launch_bounds__(kCellThreads, RR_CELL_MIN_BLOCKS) k_fallback_cells(StageArgs a) {
+  const int64_t c = a.b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int inst = -1;
+  double s = 0.0;
+  if (c < a.b.c_end) fallback_cell(a, c, inst, s);
+  // the CFL maximum of the next step (launch-uniform condition: every lane gets here)
+  if (a.stage == 3 && a.fb_pass == kFallbackPasses)
+    warp_smax(a.b.st.smax, inst, (unsigned long long)__double_as_longlong(s));
 }
 
 // ------------------------------------------------------------ constrained transport
@@ -511,14 +521,17 @@ __global__ void k_cells_from_faces(Batch b, const double* __restrict__ bface, do
 
 __global__ void k_signal(Params P, Batch b, const double* __restrict__ V) {
   const int64_t c = b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= b.c_end) return;
-  const int i = find_inst(b.cell_off, b.i_begin, b.i_end, c);
-  const InstDesc I = b.inst[i];
-  double v[NV];
-  load12(V, b.ncells, c, v);
-  double s = signal_speed(P, 0, v) / I.dx[0];
-  for (int d = 1; d < I.ndim; ++d) s = s + signal_speed(P, d, v) / I.dx[d];
-  atomicMax(b.st.smax + i, (unsigned long long)__double_as_longlong(s));
+  int i = -1;
+  double s = 0.0;
+  if (c < b.c_end) {
+    i = find_inst(b.cell_off, b.i_begin, b.i_end, c);
+    const InstDesc I = b.inst[i];
+    double v[NV];
+    load12(V, b.ncells, c, v);
+    s = signal_speed(P, 0, v) / I.dx[0];
+    for (int d = 1; d < I.ndim; ++d) s = s + signal_speed(P, d, v) / I.dx[d];
+  }
+  warp_smax(b.st.smax, i, (unsigned long long)__double_as_longlong(s));
 }
 
 // dt = CFL / max_cells sum_d lambda_d/dx_d, clipped to land on t_end.

@@ -264,28 +264,31 @@ static __device__ __noinline__ bool imp_residual(const Params& P, const ImpCell&
 }
 
 // Gaussian elimination with partial pivoting (A, b overwritten); false if singular.
-__device__ __forceinline__ bool solve4(double A[4][4], double b[4], double x[4]) {
+// T: double (the FP64 form and the matter form), or float for the matrix of the
+// FP32-bulk form's iteration on X.
+template <class T>
+__device__ __forceinline__ bool solve4(T A[4][4], T b[4], T x[4]) {
 #pragma unroll
   for (int col = 0; col < 4; ++col) {
     int piv = col;
 #pragma unroll
     for (int r = col + 1; r < 4; ++r)
       if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
-    if (A[piv][col] == 0.0) return false;
+    if (A[piv][col] == T(0)) return false;
     if (piv != col) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const double t = A[col][k];
+        const T t = A[col][k];
         A[col][k] = A[piv][k];
         A[piv][k] = t;
       }
-      const double t = b[col];
+      const T t = b[col];
       b[col] = b[piv];
       b[piv] = t;
     }
 #pragma unroll
     for (int r = col + 1; r < 4; ++r) {
-      const double f = A[r][col] / A[col][col];
+      const T f = A[r][col] / A[col][col];
 #pragma unroll
       for (int k = col + 1; k < 4; ++k) A[r][k] = A[r][k] - f * A[col][k];
       b[r] = b[r] - f * b[col];
@@ -293,7 +296,7 @@ __device__ __forceinline__ bool solve4(double A[4][4], double b[4], double x[4])
   }
 #pragma unroll
   for (int r = 3; r >= 0; --r) {
-    double s = b[r];
+    T s = b[r];
 #pragma unroll
     for (int k = r + 1; k < 4; ++k) s = s - A[r][k] * x[k];
     x[r] = s / A[r][r];
@@ -333,10 +336,54 @@ __device__ __forceinline__ void picard_matrix(const ImpCell& c, const double* X,
   }
 }
 
+// The iteration on X keeps its matrix J (an approximation of dR/dX: C^(m), the
+// cell's cache, Broyden updates, forward differences) in JT.  JT = double is the
+// FP64 form.  JT = float is the FP32-bulk form: the residual R, the iterate X and
+// every convergence test stay FP64, so the root is the FP64 root; only the Newton
+// direction is solved, and the matrix updated, in FP32.  A direction with a relative
+// error of ~1e-7 cond(J) is an inexact quasi-Newton step whose error the next FP64
+// residual corrects, as the Broyden matrix's own (larger) error is.
+
+// Newton direction dX = -J^-1 R: solved in JT, returned in double; false if singular.
+template <class JT>
+__device__ __forceinline__ bool newton_dir(const JT J[4][4], const double* R, double* dX) {
+  JT A[4][4], b[4], x[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    b[i] = (JT)(-R[i]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) A[i][j] = J[i][j];
+  }
+  if (!solve4(A, b, x)) return false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) dX[i] = (double)x[i];
+  return true;
+}
+
+// Broyden's rank-one update with the accepted step dX and residual change Rn - R:
+// J += (dR - J dX) dX^T / (dX . dX), in JT.
+template <class JT>
+__device__ __forceinline__ void broyden(JT J[4][4], const double* dXd, const double* R,
+                                        const double* Rn) {
+  JT dX[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) dX[i] = (JT)dXd[i];
+  const JT s2 = ((dX[0] * dX[0] + dX[1] * dX[1]) + dX[2] * dX[2]) + dX[3] * dX[3];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const JT dRi = (JT)(Rn[i] - R[i]);
+    const JT Jd = ((J[i][0] * dX[0] + J[i][1] * dX[1]) + J[i][2] * dX[2]) + J[i][3] * dX[3];
+    const JT q = (dRi - Jd) / s2;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) J[i][j] = J[i][j] + q * dX[j];
+  }
+}
+
 // Forward-difference Jacobian of R at X (step 1e-7 E_r; a backward step where the
 // forward one leaves the admissible set).  False if neither is admissible.
+template <class JT>
 static __device__ __noinline__ bool fd_jacobian(const Params& P, const ImpCell& c, const double* X,
-                                                const double* R, double Z, double J[4][4]) {
+                                                const double* R, double Z, JT J[4][4]) {
   const double h = 1e-7 * X[0];
   for (int j = 0; j < 4; ++j) {
     double Xp[4] = {X[0], X[1], X[2], X[3]};
@@ -348,7 +395,7 @@ static __device__ __noinline__ bool fd_jacobian(const Params& P, const ImpCell& 
     }
     const double dXj = Xp[j] - X[j];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) J[i][j] = (Rp[i] - R[i]) / dXj;
+    for (int i = 0; i < 4; ++i) J[i][j] = (JT)((Rp[i] - R[i]) / dXj);
   }
   return true;
 }
@@ -365,19 +412,14 @@ constexpr int IMP_POLISH_MAX = 6;         // at most six polishing corrections
 // halve the previous one means the rounding floor of R is reached: the polish stops
 // there without taking it.  last is the size of the converged step.  X, R, V and Z
 // stay those of the last accepted iterate.
-static __device__ __noinline__ void imp_polish(const Params& P, const ImpCell& c, double J[4][4],
+template <class JT>
+static __device__ __noinline__ void imp_polish(const Params& P, const ImpCell& c, JT J[4][4],
                                                double* X, double* R, double* V, double* Z,
                                                double last) {
   double prev = last;
   for (int p = 0; p < IMP_POLISH_MAX; ++p) {
-    double A[4][4], b[4], dX[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      b[i] = -R[i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) A[i][j] = J[i][j];
-    }
-    if (!solve4(A, b, dX)) return;
+    double dX[4];
+    if (!newton_dir(J, R, dX)) return;
     double d = 0.0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) d = fabs(dX[i]) > d ? fabs(dX[i]) : d;
@@ -387,16 +429,7 @@ static __device__ __noinline__ void imp_polish(const Params& P, const ImpCell& c
 #pragma unroll
     for (int i = 0; i < 4; ++i) Xn[i] = X[i] + dX[i];
     if (!imp_residual(P, c, Xn, *Z, Rn, Vn, &Zn)) return;
-    {  // Broyden: J += (dR - J dX) dX^T / (dX . dX)
-      const double s2 = ((dX[0] * dX[0] + dX[1] * dX[1]) + dX[2] * dX[2]) + dX[3] * dX[3];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const double Jd = ((J[i][0] * dX[0] + J[i][1] * dX[1]) + J[i][2] * dX[2]) + J[i][3] * dX[3];
-        const double q = ((Rn[i] - R[i]) - Jd) / s2;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) J[i][j] = J[i][j] + q * dX[j];
-      }
-    }
+    broyden(J, dX, R, Rn);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       X[i] = Xn[i];
@@ -416,18 +449,24 @@ static __device__ __noinline__ void imp_polish(const Params& P, const ImpCell& c
 // halvings); converged
 // when the full step is <= imp_tol * E_r, then polished (imp_polish).  Returns true
 // on convergence.
+template <class JT>
 static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c, double* X, double* R,
-                                        double* V, double* Z, const double* Min, double* Mout) {
-  double J[4][4];
+                                               double* V, double* Z, const double* Min, double* Mout) {
+  JT J[4][4];
   int need_fd = 0, fresh_fd = 0, first = 1;
   double prev = -1.0;
   if (Min) {  // the cell's matrix from its previous solve: J = I + h M
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) J[i][j] = (i == j ? 1.0 : 0.0) + c.hdt * Min[4 * i + j];
+      for (int j = 0; j < 4; ++j) J[i][j] = (JT)((i == j ? 1.0 : 0.0) + c.hdt * Min[4 * i + j]);
   } else {
-    picard_matrix(c, X, V, J);
+    double Jd[4][4];
+    picard_matrix(c, X, V, Jd);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) J[i][j] = (JT)Jd[i][j];
   }
   for (int m = 1; m <= P.imp_maxit; ++m) {
     if (need_fd) {
@@ -436,14 +475,8 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
       fresh_fd = 1;
       first = 0;
     }
-    double A[4][4], b[4], dX[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      b[i] = -R[i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) A[i][j] = J[i][j];
-    }
-    if (!solve4(A, b, dX)) {
+    double dX[4];
+    if (!newton_dir(J, R, dX)) {
       if (!fresh_fd) {
         need_fd = 1;
         continue;
@@ -470,7 +503,8 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) Mout[4 * i + j] = (J[i][j] - (i == j ? 1.0 : 0.0)) / c.hdt;
+        for (int j = 0; j < 4; ++j)
+          Mout[4 * i + j] = ((double)J[i][j] - (i == j ? 1.0 : 0.0)) / c.hdt;
       imp_polish(P, c, J, X, R, V, Z, dfull);
       return true;
     }
@@ -505,19 +539,9 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
       const double dd = fabs(dX[i]);
       if (dd > dmax) dmax = dd;
     }
-    {  // Broyden: J += (dR - J dX) dX^T / (dX . dX)
-      const double s2 = ((dX[0] * dX[0] + dX[1] * dX[1]) + dX[2] * dX[2]) + dX[3] * dX[3];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const double dRi = Rn[i] - R[i];
-        const double Jd = ((J[i][0] * dX[0] + J[i][1] * dX[1]) + J[i][2] * dX[2]) + J[i][3] * dX[3];
-        const double q = (dRi - Jd) / s2;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) J[i][j] = J[i][j] + q * dX[j];
-      }
-      fresh_fd = 0;
-      first = 0;
-    }
+    broyden(J, dX, R, Rn);
+    fresh_fd = 0;
+    first = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       X[i] = Xn[i];
@@ -669,6 +693,7 @@ __device__ __forceinline__ bool solve_matter(const Params& P, const ImpCell& c, 
 // last solve needed the matter primitives, and the next one starts there.  Order:
 // [flag 2: matter solve]; iteration on X; continuation in h on X; matter solve
 // (unless it was the first attempt).
+template <class JT = double>
 __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, double sigma,
                                              double hdt, const double* Us, double Zguess,
                                              double* U, double* V, double* jc = nullptr) {
@@ -710,7 +735,7 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
     Z = Zguess;
     imp_residual(P, c, X, Z, R, V, &Z);
   }
-  bool ok = imp_newton(P, c, X, R, V, &Z, (jc && jc[16] == 1.0) ? jc : nullptr, Mnew);
+  bool ok = imp_newton<JT>(P, c, X, R, V, &Z, (jc && jc[16] == 1.0) ? jc : nullptr, Mnew);
   if (!ok) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) X[i] = c.Xs[i];
@@ -719,7 +744,7 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
     for (int j = IMP_LADDER; j >= 0 && ok; --j) {
       c.hdt = hdt / (double)(1 << j);
       ok = imp_residual(P, c, X, Z, R, V, &Z);
-      if (ok) ok = imp_newton(P, c, X, R, V, &Z, nullptr, Mnew);
+      if (ok) ok = imp_newton<JT>(P, c, X, R, V, &Z, nullptr, Mnew);
     }
     c.hdt = hdt;
   }

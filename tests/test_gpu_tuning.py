@@ -25,6 +25,8 @@ SHAPES = [
          cell_persistent=1, lanes=16),
     dict(face_block=128, face_per_thread=2, face_persistent=0, cell_block=128, cell_per_thread=2,
          cell_persistent=0, lanes=5),
+    dict(face_block=8, face_per_thread=1, face_persistent=0, cell_block=16, cell_per_thread=1,
+         cell_persistent=0, lanes=2),
 ]
 
 
