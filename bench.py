@@ -41,17 +41,43 @@ sys.path.insert(0, ROOT)
 # of each kernel in the steady state of this workload, averaged over the three stages
 # of the 4th step (their implicit weights differ, and so does the solve's work), measured
 # with ncu on a 2048-instance sample of the same distribution.
-FP64_INST_PER_ZONE = {"fp64": {"faces": 4832.0, "cells": 4237.0},
-                      "fp32_bulk": {"faces": 4.0, "cells": 3442.0},
-                      "fp64_tangent": {"faces": 5238.0, "cells": 4244.0}}
+FP64_INST_PER_ZONE = {"fp64": {"faces": 4832.0, "cells": 4591.0},
+                      "fp32_bulk": {"faces": 4.0, "cells": 2824.0},
+                      "fp64_tangent": {"faces": 5238.0, "cells": 4591.0}}
 # DRAM bytes per cell of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
-TRAFFIC_PER_CELL = {"fp64": {"faces": 250.0, "cells": 1303.0},
-                    "fp32_bulk": {"faces": 176.0, "cells": 1277.0},
-                    "fp64_tangent": {"faces": 241.0, "cells": 1302.0}}
+TRAFFIC_PER_CELL = {"fp64": {"faces": 239.0, "cells": 1669.0},
+                    "fp32_bulk": {"faces": 174.0, "cells": 1359.0},
+                    "fp64_tangent": {"faces": 241.0, "cells": 1669.0}}
 # Nominal FP64 rate of GB300: 1.25 TFLOP/s = 6.25e11 FP64-pipe instructions/s
-# (2 per SM per clock on 152 SMs at 2.07 GHz); no MEASURED_PEAKS entry exists for FP64.
-FP64_PEAK_INST = 6.25e11
+# (2 per SM per clock on 152 SMs at 2.07 GHz).  The roofline divides by the rate
+# rrmhd_probe_fp64 measures in the same run; the nominal figure is reported beside it.
+FP64_NOMINAL_INST = 6.25e11
 BYTES_PER_ZONE_STEP = 1392.0  # minimum HBM bytes per zone-update (state in/out per stage)
+HBM_FALLBACK_GBS = 6800.0     # copy bandwidth of an earlier GB300 measurement
+
+
+def hbm_peak():
+    """Measured copy bandwidth (GB/s) of the GB300s, and where it comes from."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+def fp64_peak(skip=False):
+    """FP64-pipe rate measured now (burst: 3 x ~150 ms; sustained: 3 x ~1.5 s)."""
+    from paper_2212_00370_gb300 import rrmhd
+    if skip:
+        return {"burst": FP64_NOMINAL_INST, "sustained": FP64_NOMINAL_INST,
+                "nominal": FP64_NOMINAL_INST, "how": "not measured (--no-fp64-probe): nominal rate"}
+    burst = rrmhd.probe_fp64(150.0)
+    sustained = rrmhd.probe_fp64(1500.0)
+    return {"burst": burst, "sustained": sustained, "nominal": FP64_NOMINAL_INST,
+            "dependent_latency_ns": rrmhd.probe_fp64_latency(),
+            "how": "rrmhd_probe_fp64: 8 independent DFMA chains per thread, 2048 threads per SM "
+                   "on every SM, CUDA events, best of 3 runs of ~150 ms (burst) and ~1.5 s "
+                   "(sustained), measured in this run"}
 
 
 def parse():
@@ -69,7 +95,7 @@ def parse():
     p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32_bulk", "fp64_tangent"],
                    help="both: FP32-bulk is the headline value, FP64 (and FP64 with tangent "
                         "products) reported beside it")
-    p.add_argument("--serve-requests", type=int, default=32,
+    p.add_argument("--serve-requests", type=int, default=96,
                    help="requests of the C4 serving sample (0: skip the serving measurement)")
     p.add_argument("--serve-cells", type=int, default=4_000_000,
                    help="resident-cell bound of the serving loop (bounds its step time)")
@@ -77,6 +103,9 @@ def parse():
                    help="skip the per-step timings of the other workloads (C0 shock tube, 2D blast, 3D box)")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default launch shapes instead of autotuning them before timing")
+    p.add_argument("--no-fp64-probe", action="store_true",
+                   help="skip the FP64-pipe probe (profiling runs); the roofline then divides by "
+                        "the nominal FP64 rate")
     p.add_argument("--tuning", default=None,
                    help='fixed launch shapes as JSON, e.g. \'{"cell_block": 32, "lanes": 32}\' (no autotune)')
     return p.parse_args()
@@ -192,7 +221,7 @@ def aggregate_over_ranks(t_s, zones, world):
     return float(mx[0]), float(tt[1])
 
 
-def measure(a, precision, rank, world, local):
+def measure(a, precision, rank, world, local, peaks):
     """Time K steps of the C1 batch in one precision; returns a dict of measurements."""
     import torch
     import torch.distributed as dist
@@ -257,22 +286,32 @@ def measure(a, precision, rank, world, local):
     dom = max(groups, key=groups.get)
     per_zone = counts.get(dom)
     achieved = per_zone * zones_step / (groups[dom] / 1e3) if per_zone else None
+    kname = {"fp32_bulk": "k_cells_f32 (FP32-bulk cells: FP64 con2prim + implicit solve)",
+             "fp64": "k_cells (FP64)", "fp64_tangent": "k_cells (FP64, tangent products)"}[precision]
+    if dom == "faces":
+        kname = "k_faces_f32 (FP32-bulk faces)" if precision == "fp32_bulk" else "k_faces (FP64)"
+    hbm_gbs, hbm_src = peaks["hbm"]
+    peak = peaks["fp64"]["burst"]
     roofline = {
-        "bound": "alu", "kernel": ("k_%s" % dom) + (" (FP32 faces)" if precision == "fp32_bulk" and dom == "faces" else " (FP64)"),
-        "achieved": achieved, "peak": FP64_PEAK_INST, "unit": "FP64-pipe inst/s",
-        "frac": (achieved / FP64_PEAK_INST) if achieved else None,
+        "bound": "alu", "kernel": kname,
+        "achieved": achieved, "peak": peak, "unit": "FP64-pipe inst/s",
+        "frac": (achieved / peak) if achieved else None,
         "traffic": TRAFFIC_PER_CELL[precision].get(dom, 0) * zones_step or None,
-        "peak_source": "nominal GB300 FP64 1.25 TFLOP/s = 6.25e11 inst/s (recipe figure; "
-                       "a DFMA probe measured 5.29e11 on this pool)",
+        "peak_source": "burst rate, " + peaks["fp64"]["how"],
+        "peak_nominal": FP64_NOMINAL_INST,
+        "frac_of_nominal": (achieved / FP64_NOMINAL_INST) if achieved else None,
         "launch_ms": {"faces": round(groups["faces"], 4), "cells": round(groups["cells"], 4),
                       "fallback": round(prof[2] / 3.0, 4), "step_control": round(prof[3] / 2.0, 4)},
-        "hbm_frac": BYTES_PER_ZONE_STEP * value / (6791.7e9),
+        "hbm_frac": BYTES_PER_ZONE_STEP * value / max(world, 1) / (hbm_gbs * 1e9),
+        "hbm_peak_gbs": hbm_gbs, "hbm_peak_source": hbm_src,
     }
     # the same FP64 instruction counts over the live, lane-overlapped timed region:
-    # (faces + cells) per zone and stage x 3 stages x zone-updates/s, per GPU
+    # (faces + cells) per zone and stage x 3 stages x zone-updates/s, per GPU; a
+    # kernel inside a long step is held to the sustained rate
     live_rate = 3.0 * ((counts.get("faces") or 0.0) + counts["cells"]) * value / max(world, 1)
     roofline["live_achieved"] = live_rate
-    roofline["live_frac"] = live_rate / FP64_PEAK_INST
+    roofline["live_frac"] = live_rate / peaks["fp64"]["sustained"]
+    roofline["live_peak"] = peaks["fp64"]["sustained"]
     roofline["live_note"] = ("FP64-pipe instructions of the step's face and cell kernels per "
                              "zone-update x zone-updates/s of the timed region, per GPU; the "
                              "whole-batch launch above also carries its tail of slow solves")
@@ -285,7 +324,7 @@ def measure(a, precision, rank, world, local):
         h_in.copy_(Vdev)
         torch.cuda.synchronize()
         ctx.imex_step_host(h_in, h_out, 1)
-        ke = max(1, min(a.steps, 5))
+        ke = a.steps                         # the same K steps as the device-timed value
         t0 = time.perf_counter()
         for _ in range(ke):
             ctx.imex_step_host(h_in, h_out, 1)
@@ -344,10 +383,21 @@ def measure_variant(a, opts, tuning, steps=5):
 VARS = ["D", "Sx", "Sy", "Sz", "tau", "Bx", "By", "Bz", "E", "Fx", "Fy", "Fz"]
 
 
+def _rel_l1(a, b):
+    out = {}
+    for k in range(12):
+        den = np.abs(b[k]).sum()
+        if den > 0:
+            out[VARS[k]] = float(np.abs(a[k] - b[k]).sum() / den)
+    return out
+
+
 def measure_accuracy(a, n_inst=256, steps=5):
     """Per-variable relative L1 of the FP32-bulk form against the FP64 form (which is
     bit-identical to the oracle) on an evenly spaced sample of the C1 batch after
-    `steps` steps; instances that fail in either form are left out."""
+    `steps` steps, over the whole sample and per instance.  An instance above 1e-5 in
+    some variable is checked against the FP64 N-vs-2N difference of that instance (the
+    same problem on 2N cells run to the same time, averaged onto N)."""
     import torch
 
     from paper_2212_00370_gb300 import rrmhd
@@ -355,34 +405,62 @@ def measure_accuracy(a, n_inst=256, steps=5):
 
     w = W.riemann_batch(a.instances, seed=W.SEED_BASE + 1)
     w = w.subset(list(np.linspace(0, w.n_inst - 1, n_inst).astype(int)))
-    grids = [rrmhd.make_grid(1, g["n"], g["dx"], g["bc"]) for g in w.grids]
-    out = {}
-    for prec in ("fp32_bulk", "fp64"):
-        ctx = rrmhd.Context(grids, gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl, precision=prec)
-        ctx.set_opacity(torch.tensor(w.kappa, device="cuda"), torch.tensor(w.sigma, device="cuda"))
-        ctx.set_state(torch.tensor(w.V, device="cuda"))
-        ctx.set_times(np.zeros(w.n_inst), np.full(w.n_inst, np.inf))
-        ctx.imex_step(steps)
-        out[prec] = (ctx.get_state()[0].cpu().numpy(), ctx.inst_status())
+
+    def run(wl, prec, t_end, nsteps):
+        grids = [rrmhd.make_grid(1, g["n"], g["dx"], g["bc"]) for g in wl.grids]
+        ctx = rrmhd.Context(grids, gamma=wl.gamma, a_rad=wl.a_rad, cfl=wl.cfl, precision=prec)
+        ctx.set_opacity(torch.tensor(wl.kappa, device="cuda"), torch.tensor(wl.sigma, device="cuda"))
+        ctx.set_state(torch.tensor(wl.V, device="cuda"))
+        ctx.set_times(np.zeros(wl.n_inst), t_end)
+        ctx.imex_step(nsteps)
+        out = (ctx.get_state()[0].cpu().numpy(), ctx.inst_status(), ctx.get_times()[0])
         ctx.close()
-    (U32, s32), (U64, s64) = out["fp32_bulk"], out["fp64"]
+        return out
+
+    inf = np.full(w.n_inst, np.inf)
+    U32, s32, _ = run(w, "fp32_bulk", inf, steps)
+    U64, s64, t64 = run(w, "fp64", inf, steps)
     off = w.cell_offsets()
+    live = (s32 == 0) & (s64 == 0)
     keep = np.zeros(w.ncells, dtype=bool)
-    for i in np.nonzero((s32 == 0) & (s64 == 0))[0]:
+    above, worst = [], 0.0
+    for i in np.nonzero(live)[0]:
         keep[off[i]:off[i + 1]] = True
-    l1 = {}
-    for k in range(12):
-        den = np.abs(U64[k, keep]).sum()
-        if den > 0:
-            l1[VARS[k]] = float(np.abs(U32[k, keep] - U64[k, keep]).sum() / den)
+        e = _rel_l1(U32[:, off[i]:off[i + 1]], U64[:, off[i]:off[i + 1]])
+        worst = max(worst, max(e.values()))
+        if max(e.values()) > 1e-5:
+            above.append((int(i), e))
+    l1 = _rel_l1(U32[:, keep], U64[:, keep])
+    below = 0
+    if above:   # the FP64 N-vs-2N difference of those instances
+        parts = [w.instance(i) for i, _ in above]
+        w2 = W.Workload("C1-2N", [W.grid1d(2 * g["n"][0]) for g, *_ in parts],
+                        np.ascontiguousarray(np.concatenate([np.repeat(V, 2, axis=1) for _, V, _, _ in parts], 1)),
+                        np.concatenate([np.repeat(k, 2) for _, _, k, _ in parts]),
+                        np.concatenate([np.repeat(sg, 2) for _, _, _, sg in parts]),
+                        np.array([t64[i] for i, _ in above]), w.gamma, w.a_rad, w.cfl)
+        U2, s2, _ = run(w2, "fp64", w2.t_end, 40 * steps)
+        off2 = w2.cell_offsets()
+        for j, (i, e) in enumerate(above):
+            u2 = U2[:, off2[j]:off2[j + 1]]
+            trunc = _rel_l1(0.5 * (u2[:, 0::2] + u2[:, 1::2]), U64[:, off[i]:off[i + 1]])
+            if s2[j] == 0 and all(v < trunc[k] for k, v in e.items() if v > 1e-5):
+                below += 1
     return {"rel_l1_vs_fp64": l1, "max": max(l1.values()), "instances": int(n_inst),
-            "compared": int(((s32 == 0) & (s64 == 0)).sum()), "steps": steps,
-            "note": "FP64 form = the oracle bit for bit; bound 1e-5 per variable"}
+            "compared": int(live.sum()), "steps": steps,
+            "failed_one_form_only": int(((s32 == 0) != (s64 == 0)).sum()),
+            "failed_both": int(((s32 != 0) & (s64 != 0)).sum()),
+            "instances_above_1e-5": len(above), "of_which_below_their_n_vs_2n_difference": below,
+            "worst_instance_max_variable": worst,
+            "note": "FP64 form = the oracle bit for bit; bound per variable and instance: 1e-5, "
+                    "or below the instance's N-vs-2N difference"}
 
 
 def measure_workload(w, precision, steps, ct=0, warmup=2):
     """Per-step device times (CUDA events) of one workload in one context: zone-updates/s
-    over the timed steps and p50/p99 of the step time.  Steps stop at t_end."""
+    over the timed steps and p50/p99 of the step time.  Steps stop at t_end.  A grid of
+    fewer than 100k cells fills few SMs with the default 128-thread blocks: its launch
+    shapes are autotuned first (untimed, state restored)."""
     import torch
 
     from paper_2212_00370_gb300 import rrmhd
@@ -396,6 +474,10 @@ def measure_workload(w, precision, steps, ct=0, warmup=2):
     stream = torch.cuda.current_stream()
     ctx.imex_step(warmup)
     torch.cuda.synchronize()
+    tuning = None
+    if w.ncells < 100_000:
+        tuning, _ = ctx.autotune(repeats=3)
+        torch.cuda.synchronize()
     ms = []
     for _ in range(steps):
         t_before = ctx.get_times()[0]
@@ -415,10 +497,10 @@ def measure_workload(w, precision, steps, ct=0, warmup=2):
     return {"value": w.ncells * 1e3 * len(ms) / sum(ms), "unit": "zone-updates/s", "steps": len(ms),
             "ms_per_step": sum(ms) / len(ms), "p50_ms": float(np.percentile(ms, 50)),
             "p99_ms": float(np.percentile(ms, 99)), "cells": int(w.ncells), "precision": precision,
-            "ct": ct, "status": int(st.max())}
+            "ct": ct, "status": int(st.max()), "launch_shapes": tuning}
 
 
-def measure_others():
+def measure_others(peaks=None):
     """The other benchmark workloads, each in its own context: the C0 radiative shock
     tube (400 cells, FP64) to t_end = 0.4 after 2 warm-up steps; the 2D 1024^2 blast
     (FP32-bulk, constrained transport) and the 3D 256^3 box (FP32-bulk and FP64,
@@ -426,6 +508,13 @@ def measure_others():
     from paper_2212_00370_gb300 import workloads as W
     out = {}
     out["shock_tube_400_fp64"] = measure_workload(W.shock_tube(400), "fp64", 1000)
+    lat = (peaks or {}).get("fp64", {}).get("dependent_latency_ns")
+    if lat:
+        out["shock_tube_400_fp64"]["bound"] = (
+            "FP64 dependent-instruction latency: 400 cells make ~13 warps, one per SM, and a "
+            "dependent FP64 instruction of one warp takes %.1f ns (rrmhd_probe_fp64_latency); "
+            "the per-cell Newton chains are serial, so block shapes do not change the step "
+            "time" % lat)
     c2 = W.blast_2d()
     out["blast_2d_1024x1024_fp32_bulk_ct"] = measure_workload(c2, "fp32_bulk", 20, ct=1)
     c3 = W.turbulent_3d()
@@ -459,13 +548,15 @@ def measure_serving(a, tuning=None):
                        max_resident_cells=a.serve_cells, tuning=tuning)
     srv.wait_idle(1.0)
 
+    index_of = {}
+
     def submitter():
         t0 = time.perf_counter()
-        for sp, g, (gd, V, k, sg, te) in zip(specs, grids, reqs):
+        for k, (sp, g, (gd, V, kp, sg, te)) in enumerate(zip(specs, grids, reqs)):
             delay = sp["arrival"] - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            srv.submit(g, V, k, sg, te)
+            index_of[srv.submit(g, V, kp, sg, te)] = k
 
     th = threading.Thread(target=submitter)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
@@ -481,14 +572,25 @@ def measure_serving(a, tuning=None):
     ok = [r for r, _ in results if r["status"] == 0]
     tts = np.array([r["done_s"] - r["submit_s"] for r in ok])
     service = np.array([r["done_s"] - r["admit_s"] for r in ok])
+    queueing = np.array([r["admit_s"] - r["submit_s"] for r in ok])
     span = max(r["done_s"] for r, _ in results) - min(r["submit_s"] for r, _ in results)
+
+    def pct(x, q):
+        return float(np.percentile(x, q)) if len(x) else None
     return {
         "workload": "C4 sample: first %d requests of Poisson arrivals at %.0f/s (70%% 1D N~U{256..4096}, "
                     "30%% planar 2D side~U{128..512}, C1 states, t_end 0.2, FP32-bulk, CT for 2D)" % (n_req, rate),
         "requests": n_req, "completed": len(results), "failed": len(results) - len(ok),
-        "p50_tts_s": float(np.percentile(tts, 50)) if len(tts) else None,
-        "p99_tts_s": float(np.percentile(tts, 99)) if len(tts) else None,
-        "p50_service_s": float(np.percentile(service, 50)) if len(service) else None,
+        "failed_requests": [{"index": index_of.get(r["id"]), "ndim": specs[index_of[r["id"]]]["ndim"],
+                             "size": specs[index_of[r["id"]]]["size"], "status": r["status"],
+                             "steps": r["steps"], "t": r["t"]}
+                            for r, _ in results if r["status"] != 0 and r["id"] in index_of],
+        "p50_tts_s": pct(tts, 50), "p99_tts_s": pct(tts, 99),
+        "p50_service_s": pct(service, 50), "p99_service_s": pct(service, 99),
+        "p50_queueing_s": pct(queueing, 50), "p99_queueing_s": pct(queueing, 99),
+        "arrival_window_s": specs[-1]["arrival"] - specs[0]["arrival"],
+        "sample_offered_zone_updates_per_s_at_most":
+            sum(zu_max(sp) for sp in specs) / max(specs[-1]["arrival"] - specs[0]["arrival"], 1e-9),
         "zone_updates_per_s": st["zone_updates"] / span, "zone_updates": st["zone_updates"],
         "makespan_s": span, "server_steps": st["steps"], "relayouts": st["relayouts"],
         "resident_cell_bound": st["cap_cells"], "peak_resident_cells": st["peak_resident_cells"],
@@ -510,7 +612,9 @@ def run_ours(a, rank, world, pool, cores):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     precisions = ["fp32_bulk", "fp64", "fp64_tangent"] if a.precision == "both" else [a.precision]
-    res = {p: measure(a, p, rank, world, local) for p in precisions}
+    from paper_2212_00370_gb300 import rrmhd  # noqa: F401  (loads the library)
+    peaks = {"fp64": fp64_peak(a.no_fp64_probe), "hbm": hbm_peak()}
+    res = {p: measure(a, p, rank, world, local, peaks) for p in precisions}
     head = res[precisions[0]]
     out = {
         "metric": "zone-updates/s per IMEX step (FP32-bulk vs FP64, 1 GB300; % of roofline; p50/p99 step time)",
@@ -528,7 +632,7 @@ def run_ours(a, rank, world, pool, cores):
                    "l2": "state %.0f MB per copy > 129 MB L2 (inputs larger than L2)" % head["ncells_state_mb"]},
         "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
         "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
-        "clocks": head["clocks"],
+        "clocks": head["clocks"], "fp64_peak": peaks["fp64"],
     }
     if len(precisions) > 1:
         f = res["fp64"]
@@ -556,7 +660,7 @@ def run_ours(a, rank, world, pool, cores):
                             "C1 batch; the paper reports PVM-int-8 costing ~2x HLL in CPU time")
         out["fp64_variants"] = variants
     if not a.no_others and world == 1:
-        out["other_workloads"] = measure_others()
+        out["other_workloads"] = measure_others(peaks)
     if a.serve_requests > 0 and world == 1:
         out["serving"] = measure_serving(a, res["fp32_bulk"]["tuning"] if "fp32_bulk" in res else None)
     if rank == 0 and pool is not None:

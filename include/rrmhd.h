@@ -221,7 +221,9 @@ int rrmhd_launches_per_step(const rrmhd_ctx* ctx);
  * concurrent lanes a context splits its instances.  Shapes never change results:
  * every face and cell is computed once, by the same arithmetic, whatever the
  * shape (bit-identical output).
- *   *_block        threads per block: 32, 64, 128 or 256
+ *   *_block        threads per block: 32, 64, 128 or 256; also 8 or 16 for the
+ *                  grid schedule with one item per thread (partial warps: a small
+ *                  grid spread over more SMs)
  *   *_per_thread   faces or cells per thread of the grid schedule: 1 or 2
  *   *_persistent   1: a resident grid (SMs x resident blocks per SM) whose warps take
  *                  chunks of 32 consecutive items from a counter until none are
@@ -266,6 +268,25 @@ rrmhd_status rrmhd_get_face_field(const rrmhd_ctx* ctx, double* b);
 /* rho h W^2 of primitives: V double[12][n] -> Z double[n] (con2prim warm starts). */
 rrmhd_status rrmhd_prim_z(rrmhd_ctx* ctx, const double* V, double* Z, int64_t n);
 
+/* ---- FP64 throughput probe (not a step of the method) ------------------------
+ * The cell and face kernels are bound by the FP64 pipe; this measures that pipe's
+ * rate on the current device, the denominator of their roofline.  Every thread of
+ * 8 blocks of 256 per SM runs eight independent DFMA chains (the pipe, not one
+ * chain's latency, is the limit); a short run calibrates the trip count so that one
+ * run takes about target_ms (host, ms, in (0, 10000]); the best of three runs, timed
+ * with CUDA events on cuda_stream (NULL = legacy default), is returned in
+ * *inst_per_s (host): thread-level FP64 instructions per second, the unit of the
+ * ncu counters sm__sass_thread_inst_executed_op_d{add,mul,fma}.  Synchronises the
+ * stream.  EINVAL for a bad argument, ECUDA if a launch or event fails. */
+rrmhd_status rrmhd_probe_fp64(void* cuda_stream, double target_ms, double* inst_per_s);
+
+/* Latency of a dependent FP64 instruction: one warp, one chain of 65,536 dependent
+ * DFMA per thread, best of three runs timed with CUDA events on cuda_stream; *ns_per_inst
+ * (host) receives nanoseconds per instruction.  This is what bounds a grid too small
+ * to put several warps on every SM.  Synchronises the stream.  EINVAL for a NULL
+ * output, ECUDA if a launch or event fails. */
+rrmhd_status rrmhd_probe_fp64_latency(void* cuda_stream, double* ns_per_inst);
+
 /* ---- Alloc-free entry point (no counterpart in the paper) ----------------
  * For callers that cannot allocate device memory themselves, e.g. a host program
  * whose GPU memory is all owned by its own pool or fixed arena, reserved at
@@ -280,8 +301,9 @@ rrmhd_status rrmhd_prim_z(rrmhd_ctx* ctx, const double* V, double* Z, int64_t n)
  * (about 32 KB), present on every GPU that loads the library until the process
  * exits.  It holds up to RRMHD_NOALLOC_MAX_CELLS cells; larger grids return
  * RRMHD_ECAPACITY before any work is enqueued.  The first call on a device looks
- * up the scratch's device address (once per device); make that first call
- * before any stream capture.  All calls on a device share the one scratch array
+ * up the scratch's device address and keeps it for the life of the process; make
+ * that first call before any stream capture (a lookup that fails returns ECUDA
+ * and is tried again by the next call).  All calls on a device share the one scratch array
  * (each call first resets the part that must start at zero): calls that overlap
  * on the GPU -- on different streams, or from different host threads without
  * ordering -- race and return wrong values.  A NaN signal speed gives dt = NaN.

@@ -26,6 +26,7 @@ UNITS = {
     "rrmhd_noalloc.cu": ["--fmad=false"],
     "rrmhd_f32.cu": [],
     "rrmhd_server.cu": ["--fmad=false"],
+    "rrmhd_probe.cu": [],
 }
 HEADERS = ["physics_f64.cuh", "scheme_f64.cuh", "physics_tangent.cuh", "batch.h", "batch_index.cuh",
            "engine.h"]

@@ -109,6 +109,8 @@ _SIGNATURES = [
     ("rrmhd_autotune", C.c_int, [_VP, C.c_int, C.POINTER(rrmhd_tuning), _DP]),
     ("rrmhd_set_face_field", C.c_int, [_VP, _VP]),
     ("rrmhd_get_face_field", C.c_int, [_VP, _VP]),
+    ("rrmhd_probe_fp64", C.c_int, [_VP, C.c_double, _DP]),
+    ("rrmhd_probe_fp64_latency", C.c_int, [_VP, _DP]),
     ("rrmhd_cfl_dt_noalloc", C.c_int, [C.POINTER(rrmhd_grid), C.POINTER(rrmhd_opts), _VP, _VP, _VP]),
     ("rrmhd_server_create", C.c_int, [C.POINTER(rrmhd_opts), C.POINTER(rrmhd_server_config),
                                       C.POINTER(_VP)]),
@@ -353,6 +355,21 @@ class Context:
             self.ctx, float(hdt), _ptr(Ustar.contiguous()),
             _ptr(None if Zguess is None else Zguess.contiguous()), _ptr(U), _ptr(V), _ptr(st)))
         return U, V, st
+
+
+def probe_fp64(target_ms=100.0, stream=None):
+    """FP64-pipe rate of the current device (rrmhd_probe_fp64): thread-level FP64
+    instructions per second of independent DFMA chains on every SM."""
+    out = C.c_double()
+    _check(None, lib().rrmhd_probe_fp64(_stream(stream), float(target_ms), C.byref(out)))
+    return out.value
+
+
+def probe_fp64_latency(stream=None):
+    """Nanoseconds per dependent FP64 instruction of one warp (rrmhd_probe_fp64_latency)."""
+    out = C.c_double()
+    _check(None, lib().rrmhd_probe_fp64_latency(_stream(stream), C.byref(out)))
+    return out.value
 
 
 def server_admission(cells, faces, free_cells, free_faces, free_slots):
