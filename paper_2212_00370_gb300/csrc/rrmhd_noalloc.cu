@@ -35,21 +35,23 @@ static __device__ __align__(256) Scratch g_cfl_scratch;
 
 constexpr int kMaxDevices = 64;
 Scratch* g_scratch_ptr[kMaxDevices] = {};
-std::once_flag g_scratch_once[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices] = {};
+std::mutex g_scratch_mu[kMaxDevices];
 
-// Device address of g_cfl_scratch on the current device (set up once per device).
+// Device address of g_cfl_scratch on the current device.  The first successful
+// lookup is kept for the life of the process; a failed one (for instance a first
+// call made during stream capture) is not, and the next call looks it up again.
 cudaError_t scratch_on_current_device(Scratch** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::call_once(g_scratch_once[dev], [dev] {
+  std::lock_guard<std::mutex> lock(g_scratch_mu[dev]);
+  if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
-    g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_cfl_scratch);
-    if (g_scratch_err[dev] == cudaSuccess) g_scratch_ptr[dev] = static_cast<Scratch*>(p);
-  });
-  if (g_scratch_err[dev] != cudaSuccess) return g_scratch_err[dev];
+    e = cudaGetSymbolAddress(&p, g_cfl_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = static_cast<Scratch*>(p);
+  }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;
 }

@@ -49,3 +49,25 @@ def compare_bitwise(a, b, what):
     rel = np.where(diff, np.abs(a - b) / np.where(scale > 0, scale, 1), 0)
     raise AssertionError(f"{what}: {diff.sum()} of {diff.size} values differ; max rel "
                          f"{rel.max():.3e}; first at {idx.tolist()}")
+
+
+def _oracle_job(job):
+    """Worker of oracle_pool_runs: (n, dx, V, kappa, sigma, gamma, a_rad, cfl, t_end,
+    max_steps) of one 1D outflow instance -> (U, V, t, steps, nfail)."""
+    n, dx, V, kappa, sigma, gamma, a_rad, cfl, t_end, max_steps = job
+    P = O.Params(gamma=gamma, a_rad=a_rad, cfl=cfl)
+    V = np.ascontiguousarray(V, dtype=np.float64).copy()
+    U = O.prim2con(V, P)
+    t, steps, nfail = O.run(O.Grid(1, (int(n),), (float(dx),)), 0.0, float(t_end), U, V,
+                            np.ascontiguousarray(kappa), np.ascontiguousarray(sigma), P,
+                            max_steps=int(max_steps))
+    return U, V, t, steps, nfail
+
+
+def oracle_pool_runs(jobs, processes=None):
+    """Run oracle jobs (see _oracle_job) in a spawn pool (safe after CUDA is initialised)."""
+    import multiprocessing as mp
+    import os
+    processes = processes or min(len(jobs), os.cpu_count() or 1, 32)
+    with mp.get_context("spawn").Pool(processes) as pool:
+        return pool.map(_oracle_job, jobs, chunksize=1)

@@ -79,18 +79,59 @@ def test_fp32_bulk_c0_to_t_end_within_bounds():
 
 
 def test_fp32_bulk_c1_steps():
-    w = W.riemann_batch(40, seed=23, nmin=20, nmax=200)
+    """The headline batch (C1, 4096 instances, seed 2212003701): 256 instances spread
+    evenly over it, 5 steps of the FP32-bulk form against 5 steps of the FP64 oracle.
+    Every instance must meet the bound per variable (relative L1 <= 1e-5); an instance
+    above it must instead be below the oracle's own N-vs-2N difference for that
+    instance (the same problem on 2N cells run to the same time, averaged onto N) in
+    every variable above 1e-5.  Such instances are counted and printed.  An instance
+    that fails in one form and not in the other fails the test."""
+    from gpu_helpers import oracle_pool_runs
+    full = W.riemann_batch(4096, seed=W.SEED_BASE + 1)
+    w = full.subset(list(np.linspace(0, full.n_inst - 1, 256).astype(int)))
     ctx = gpu_context(w, precision="fp32_bulk")
+    ctx.set_times(np.zeros(w.n_inst), np.full(w.n_inst, np.inf))
     ctx.imex_step(5)
     U32 = ctx.get_state()[0].cpu().numpy()
     st = ctx.inst_status()
     off = w.cell_offsets()
-    worst = {}
+    jobs = []
     for i in range(w.n_inst):
-        Ur, Vr, tr, steps, nfail = oracle_run_instance(w, i, 5)
-        if nfail or st[i]:
+        g, V, kappa, sigma = w.instance(i)
+        jobs.append((g["n"][0], g["dx"][0], V, kappa, sigma, w.gamma, w.a_rad, w.cfl, np.inf, 5))
+    ref = oracle_pool_runs(jobs)
+    mismatch = [i for i in range(w.n_inst) if (ref[i][4] != 0) != (st[i] != 0)]
+    both_failed = [i for i in range(w.n_inst) if ref[i][4] != 0 and st[i] != 0]
+    worst, above = {}, []
+    for i in range(w.n_inst):
+        if i in both_failed:
             continue
-        for k, v in rel_l1(U32[:, off[i]:off[i + 1]], Ur).items():
+        e = rel_l1(U32[:, off[i]:off[i + 1]], ref[i][0])
+        for k, v in e.items():
             worst[k] = max(worst.get(k, 0.0), v)
-    print("C1 5 steps, worst per-variable rel L1:", {k: "%.2e" % v for k, v in worst.items()})
-    assert max(worst.values()) < 1e-3
+        if max(e.values()) > 1e-5:
+            above.append((i, e))
+    # the oracle's N-vs-2N difference of the instances above the bound
+    jobs2 = []
+    for i, _ in above:
+        g, V, kappa, sigma = w.instance(i)
+        jobs2.append((2 * g["n"][0], 0.5 * g["dx"][0], np.repeat(V, 2, axis=1), np.repeat(kappa, 2),
+                      np.repeat(sigma, 2), w.gamma, w.a_rad, w.cfl, ref[i][2], 10 ** 6))
+    bad = []
+    for (i, e), r2 in zip(above, oracle_pool_runs(jobs2) if jobs2 else []):
+        assert r2[4] == 0 and r2[2] == pytest.approx(ref[i][2], rel=1e-12), (i, r2[2], ref[i][2])
+        U2c = 0.5 * (r2[0][:, 0::2] + r2[0][:, 1::2])
+        trunc = rel_l1(U2c, ref[i][0])
+        over = {k: (v, trunc[k]) for k, v in e.items() if v > 1e-5 and not v < trunc[k]}
+        print("instance %d (%d cells): FP32-bulk %s | N vs 2N %s" % (
+            i, w.grids[i]["n"][0], {k: "%.1e" % v for k, v in e.items() if v > 1e-5},
+            {k: "%.1e" % trunc[k] for k, v in e.items() if v > 1e-5}))
+        if over:
+            bad.append((i, over))
+    print("C1 256 instances x 5 steps, worst per-variable rel L1:",
+          {k: "%.2e" % v for k, v in worst.items()})
+    print("instances above 1e-5: %d (all below their N-vs-2N difference: %s); failed in both "
+          "forms: %d; failed in one form only: %d" % (len(above), not bad, len(both_failed), len(mismatch)))
+    assert not mismatch, mismatch
+    assert not bad, bad
+    assert len(both_failed) <= 2, both_failed

@@ -72,3 +72,17 @@ def test_noalloc_cfl_rejects_oversized_grids():
     assert rrmhd.STATUS[rc] == "ECAPACITY"
     rc = rrmhd.lib().rrmhd_cfl_dt_noalloc(C.byref(grid), C.byref(opts), None, p, None)
     assert rrmhd.STATUS[rc] == "EINVAL"
+
+
+def test_noalloc_cfl_nan_cell_gives_nan_dt():
+    """A NaN radiation energy makes both radiation speeds of its cell NaN, and so its
+    signal speed, which wins the maximum: dt = NaN on two calls in a row, and the
+    next admissible grid gets its own dt again (nothing of the NaN stays in the
+    shared scratch)."""
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    w = W.shock_tube(400)
+    bad = W.shock_tube(400)
+    bad.V = bad.V.copy()
+    bad.V[8, 123] = np.nan
+    assert np.isnan(_noalloc_dt(bad, out)) and np.isnan(_noalloc_dt(bad, out))
+    assert _noalloc_dt(w, out) == _context_dt(w)
