@@ -195,14 +195,17 @@ def serving_requests(n_req, rate=200.0, seed=SEED_BASE + 4, frac_1d=0.7, n1d=(25
     """C4 arrival process: n_req requests with exponential inter-arrival times of
     mean 1/rate seconds; each is 1D with probability frac_1d (N ~ U{n1d}) or a
     planar 2D problem (side ~ U{side2d}).  Returns light specs (arrival time, kind,
-    size, per-request seed); ``serving_request`` draws the arrays of one spec."""
+    size, per-request seed); ``serving_request`` draws the arrays of one spec.  The
+    draws are made request by request, so the first k requests of any n_req >= k are
+    the same: a sample of n_req is the start of the full process."""
     rng = np.random.default_rng(seed)
-    t = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    t = 0.0
     specs = []
     for k in range(n_req):
+        t = t + float(rng.exponential(1.0 / rate))
         one_d = rng.uniform() < frac_1d
         size = int(rng.integers(n1d[0], n1d[1] + 1)) if one_d else int(rng.integers(side2d[0], side2d[1] + 1))
-        specs.append({"arrival": float(t[k]), "ndim": 1 if one_d else 2, "size": size,
+        specs.append({"arrival": t, "ndim": 1 if one_d else 2, "size": size,
                       "seed": int(rng.integers(2 ** 62)), "t_end": float(t_end)})
     return specs
 

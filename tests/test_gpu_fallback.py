@@ -111,7 +111,7 @@ def test_ct_fallback_outflow_strip_bitwise():
     415 x 4 strip, with constrained transport, 60 steps: the fallback fires next
     to the outflow boundaries, its Rusanov fluxes enter the edge EMFs, and the
     3x3 block around each flagged cell is updated again.  Bit for bit."""
-    spec = W.serving_requests(32, rate=200.0)[12]
+    spec = {"ndim": 2, "size": 415, "seed": 1705737974979711427, "t_end": 0.2, "arrival": 0.0}
     g0, V0, k0, s0, _ = W.serving_request(spec)
     n, ny = g0["n"][0], 4
     g = {"ndim": 2, "n": (n, ny, 1), "dx": (1.0 / n, 1.0 / n, 1.0), "bc": ("outflow",) * 3}

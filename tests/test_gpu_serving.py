@@ -29,11 +29,24 @@ def _built():
     build.build()
 
 
+def small_specs(n, seed, frac_1d=0.6, n1d=(16, 300), side2d=(8, 24), t_end=0.04):
+    """Specs of n small requests (all at once): the n arrival draws first, then kind,
+    size and seed per request.  The cases below (which requests are 2D, which fall
+    back, where constrained transport changes the update) are those of these draws."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1e-6, n))
+    specs = []
+    for k in range(n):
+        one_d = rng.uniform() < frac_1d
+        size = int(rng.integers(n1d[0], n1d[1] + 1)) if one_d else int(rng.integers(side2d[0], side2d[1] + 1))
+        specs.append({"arrival": float(t[k]), "ndim": 1 if one_d else 2, "size": size,
+                      "seed": int(rng.integers(2 ** 62)), "t_end": float(t_end)})
+    return specs
+
+
 def small_requests(n, seed, t_end=0.04):
     """A mix of small 1D (16..300 cells) and planar 2D (8^2..24^2) requests with C1 states."""
-    specs = W.serving_requests(n, rate=1e6, seed=seed, frac_1d=0.6, n1d=(16, 300), side2d=(8, 24),
-                               t_end=t_end)
-    return [W.serving_request(s) for s in specs]
+    return [W.serving_request(s) for s in small_specs(n, seed, t_end=t_end)]
 
 
 def grid_of(g):
