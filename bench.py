@@ -87,10 +87,14 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--instances", type=int, default=4096)
+    p.add_argument("--workload", default="c1", choices=["c1", "c0"],
+                   help="c1: the 4096-instance batch (the headline); c0: the 400-cell radiative "
+                        "shock tube alone (FP64, to t_end), a latency-bound small grid")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-sample", type=int, default=4096,
-                   help="instances in the CPU sample (1 step each; default: the whole batch)")
+    p.add_argument("--cpu-sample", type=int, default=None,
+                   help="instances in the CPU sample (default: 1024 for the cpu_baseline leg, "
+                        "the whole batch for --impl reference)")
     p.add_argument("--lanes", type=int, default=8, help="independent sub-batches (streams)")
     p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32_bulk", "fp64_tangent"],
                    help="both: FP32-bulk is the headline value, FP64 (and FP64 with tangent "
@@ -123,18 +127,43 @@ def _worker_init(seed, n_inst):
     _WORKER["w"] = W.riemann_batch(n_inst, seed=seed)
 
 
-def _oracle_instance_steps(args):
-    """Worker: advance one instance by nsteps with the oracle; returns zone-updates done."""
-    idx, nsteps = args
+def _oracle_slice_steps(args):
+    """Worker: the instances of one fixed slice, `warm` untimed steps, then `steps`
+    timed steps of the whole slice (each instance keeps its state and Jacobian cache
+    from step to step, as a run does).  Returns the wall time and the zone-updates of
+    every timed step (a failed instance stops contributing)."""
+    idx, warm, steps = args
     import oracle as O
     w = _WORKER["w"]
-    g, V, kappa, sigma = w.instance(idx)
     P = O.Params(gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl)
-    V = np.ascontiguousarray(V).copy()
-    U = O.prim2con(V, P)
-    grid = O.Grid(1, (g["n"][0],), (g["dx"][0],))
-    t, steps, nfail = O.run(grid, 0.0, np.inf, U, V, kappa, sigma, P, max_steps=nsteps)
-    return g["n"][0] * steps if not nfail else 0
+    insts = []
+    for i in idx:
+        g, V, kappa, sigma = w.instance(int(i))
+        V = np.ascontiguousarray(V).copy()
+        grid = O.Grid(1, (g["n"][0],), (g["dx"][0],))
+        insts.append([grid, O.prim2con(V, P), V, kappa, sigma, np.zeros(17 * g["n"][0]), True])
+
+    def one_step():
+        zones = 0
+        for it in insts:
+            grid, U, V, kappa, sigma, jc, ok = it
+            if not ok:
+                continue
+            dt = O.grid_dt(grid, V, P)
+            if not (dt > 0) or O.step(grid, dt, U, V, kappa, sigma, P, jcache=jc):
+                it[6] = False
+                continue
+            zones += grid.ncells
+        return zones
+
+    for _ in range(warm):
+        one_step()
+    times, zones = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        zones.append(one_step())
+        times.append(time.perf_counter() - t0)
+    return times, zones
 
 
 def make_pool(cores, seed, n_inst):
@@ -147,15 +176,18 @@ def _noop(x):
     return x
 
 
-def cpu_oracle(pool, cores, seed, n_inst, sample, nsteps):
-    """Oracle throughput on `sample` instances (evenly spread over the batch), `nsteps`
-    steps each, over `cores` worker processes.  Returns (zone-updates/s, wall s, zones)."""
+def cpu_oracle(pool, cores, n_inst, sample, warm, steps):
+    """Oracle throughput on `sample` instances evenly spread over the batch, split into
+    `cores` fixed slices (one per worker process, running concurrently): `warm` untimed
+    steps, then `steps` timed steps, the steady state the GPU arm times.  A step's wall
+    time is that of the slowest slice.  Returns (zone-updates/s, per-step wall times in
+    s, zone-updates)."""
     idx = np.linspace(0, n_inst - 1, sample).astype(int)
-    t0 = time.perf_counter()
-    res = pool.map(_oracle_instance_steps, [(int(i), nsteps) for i in idx], chunksize=1)
-    wall = time.perf_counter() - t0
-    zones = sum(res)
-    return zones / wall, wall, zones
+    slices = [idx[k::cores] for k in range(cores)]
+    res = pool.map(_oracle_slice_steps, [(sl, warm, steps) for sl in slices], chunksize=1)
+    walls = [max(r[0][k] for r in res) for k in range(steps)]
+    zones = sum(sum(r[1]) for r in res)
+    return zones / sum(walls), walls, zones
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -604,6 +636,29 @@ def measure_serving(a, tuning=None):
 
 
 DTYPE = {"fp64": "f64", "fp32_bulk": "f32 faces + f64 cells", "fp64_tangent": "f64"}
+METRIC = "zone-updates/s per IMEX step (FP32-bulk vs FP64, 1 GB300; % of roofline; p50/p99 step time)"
+
+
+def workload_name(n_inst):
+    return ("C1: %d independent 1D RRMHD Riemann problems per GPU, N~U{128..2048}, seed "
+            "2212003701+rank, gamma 4/3, PVM-int-8 + VanLeer + IMEX-RK3" % n_inst)
+
+
+def run_c0(a):
+    """The C0 shock tube alone: per-step device times to t_end, and the FP64 latency
+    probe that bounds it."""
+    from paper_2212_00370_gb300 import rrmhd
+    from paper_2212_00370_gb300 import workloads as W
+    r = measure_workload(W.shock_tube(400), "fp64", 1000, warmup=a.warmup)
+    lat = None if a.no_fp64_probe else rrmhd.probe_fp64_latency()
+    return {"metric": "zone-updates/s per IMEX step (C0 shock tube, 400 cells, FP64)",
+            "value": r.get("value"), "unit": "zone-updates/s", "n_gpus": 1, "steps": r.get("steps"),
+            "warmup": a.warmup, "ms_per_step": r.get("ms_per_step"), "p50_ms": r.get("p50_ms"),
+            "p99_ms": r.get("p99_ms"), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "C0: 1D radiative shock tube, 400 cells, gamma 5/3, kappa 1, to t_end 0.4",
+                       "launch_shapes": r.get("launch_shapes")},
+            "fp64_dependent_latency_ns": lat}
 
 
 def run_ours(a, rank, world, pool, cores):
@@ -611,19 +666,19 @@ def run_ours(a, rank, world, pool, cores):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if a.workload == "c0":
+        return run_c0(a)
     precisions = ["fp32_bulk", "fp64", "fp64_tangent"] if a.precision == "both" else [a.precision]
     from paper_2212_00370_gb300 import rrmhd  # noqa: F401  (loads the library)
     peaks = {"fp64": fp64_peak(a.no_fp64_probe), "hbm": hbm_peak()}
     res = {p: measure(a, p, rank, world, local, peaks) for p in precisions}
     head = res[precisions[0]]
     out = {
-        "metric": "zone-updates/s per IMEX step (FP32-bulk vs FP64, 1 GB300; % of roofline; p50/p99 step time)",
+        "metric": METRIC,
         "value": head["value"], "unit": "zone-updates/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[precisions[0]], "data": "synthetic",
-        "config": {"workload": "C1: %d independent 1D RRMHD Riemann problems per GPU, N~U{128..2048}, "
-                               "seed 2212003701+rank, gamma 4/3, PVM-int-8 + VanLeer + IMEX-RK3, "
-                               "precision %s" % (a.instances, precisions[0]),
+        "config": {"workload": workload_name(a.instances), "precision": precisions[0],
                    "instances": a.instances, "cells": head["cells"],
                    "live_instances": head["live"], "failed_instances": head["failed"],
                    "parallelism": "replicas (independent problems per GPU); %d lanes (streams) per GPU"
@@ -664,45 +719,41 @@ def run_ours(a, rank, world, pool, cores):
     if a.serve_requests > 0 and world == 1:
         out["serving"] = measure_serving(a, res["fp32_bulk"]["tuning"] if "fp32_bulk" in res else None)
     if rank == 0 and pool is not None:
-        zps, wall, zc = cpu_oracle(pool, cores, head["seed"], a.instances, a.cpu_sample, 1)
+        from paper_2212_00370_gb300 import workloads as W
+        zps, walls, zc = cpu_oracle(pool, cores, a.instances, a.cpu_sample, 2, 2)
         out["cpu_baseline"] = {"value": zps, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
-                               "sample": "%d of the %d instances (evenly spaced), 1 step each, %d zone-updates, %.1f s wall"
-                                         % (a.cpu_sample, a.instances, zc, wall)}
+                               "sample": "%d of the %d instances (evenly spaced, seed %d), 2 untimed warm-up "
+                                         "steps, then 2 timed steps: %d zone-updates in %.1f s wall"
+                                         % (a.cpu_sample, a.instances, W.SEED_BASE + 1, zc, sum(walls))}
     return out
 
 
 def run_reference(a, rank, pool, cores):
-    from paper_2212_00370_gb300 import workloads as W
-    seed = W.SEED_BASE + 1
-    for _ in range(a.warmup):
-        cpu_oracle(pool, cores, seed, a.instances, max(cores, 8), 1)
-    vals = []
-    t0 = time.perf_counter()
-    zones = 0
-    for _ in range(a.steps):
-        zps, wall, zc = cpu_oracle(pool, cores, seed, a.instances, a.cpu_sample, 1)
-        vals.append(wall)
-        zones += zc
-    wall = time.perf_counter() - t0
-    value = zones / wall
+    """The reference arm: the FP64 CPU oracle on the host cores, on the same C1 batch,
+    steady state as the GPU arm times it (W untimed steps, then K timed steps of the
+    sampled instances)."""
+    zps, walls, zones = cpu_oracle(pool, cores, a.instances, a.cpu_sample, a.warmup, a.steps)
     return {
         "impl": "reference",
-        "metric": "zone-updates/s per IMEX step (FP32-bulk vs FP64, 1 GB300; % of roofline; p50/p99 step time)",
-        "value": value, "unit": "zone-updates/s", "n_gpus": 0, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": 1e3 * wall / a.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC,
+        "value": zps, "unit": "zone-updates/s", "n_gpus": 0, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * sum(walls) / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "C1: %d independent 1D RRMHD Riemann problems, FP64 CPU oracle; each step "
-                               "is a sample of %d instances" % (a.instances, a.cpu_sample),
-                   "instances": a.instances},
-        "cpu_baseline": {"value": value, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d instances per step, 1 IMEX step each" % a.cpu_sample},
-        "e2e": {"value": value, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "p50_ms": float(np.percentile(vals, 50) * 1e3), "p99_ms": float(np.percentile(vals, 99) * 1e3),
+        "config": {"workload": workload_name(a.instances), "precision": "fp64 (CPU oracle)",
+                   "instances": a.instances, "sampled_instances": a.cpu_sample},
+        "cpu_baseline": {"value": zps, "unit": "zone-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d of the %d instances (evenly spaced), %d untimed warm-up steps, "
+                                   "then %d timed steps, one fixed slice per core"
+                                   % (a.cpu_sample, a.instances, a.warmup, a.steps)},
+        "e2e": {"value": zps, "unit": "zone-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "p50_ms": float(np.percentile(walls, 50) * 1e3), "p99_ms": float(np.percentile(walls, 99) * 1e3),
     }
 
 
 def main():
     a = parse()
+    if a.cpu_sample is None:
+        a.cpu_sample = a.instances if a.impl == "reference" else min(1024, a.instances)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
@@ -710,7 +761,7 @@ def main():
     OB.build()
     pool = None
     # the oracle pool is started (spawn) before the first GPU call, on rank 0 only
-    if rank == 0 and (a.impl == "reference" or not a.no_cpu):
+    if rank == 0 and (a.impl == "reference" or (not a.no_cpu and a.workload == "c1")):
         from paper_2212_00370_gb300 import workloads as W
         pool = make_pool(cores, W.SEED_BASE + 1, a.instances)
     try:
