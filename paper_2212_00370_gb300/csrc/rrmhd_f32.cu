@@ -22,6 +22,18 @@ using namespace idx;
 constexpr int kFaceThreads = 128;
 constexpr int kCellThreads = 128;
 
+// Resident warps per SM the cell kernels are compiled for (a register bound of
+// 65536 / (32 x warps) per thread).  12 warps (168 registers; the solver's stack grows
+// from 1.5 to 1.9 KB) hide more of the FP64 dependency latency than the 8 that 255
+// registers allow: +2 % zone-updates/s on C1 in the live step, measured under three
+// cell shapes; 16 warps (128 registers) gained nothing.
+#ifndef RR_F32_CELL_WARPS
+#define RR_F32_CELL_WARPS 12
+#endif
+// (at most 32 resident blocks per SM: partial-warp blocks of 8 threads keep no bound)
+#define RR_F32_CELL_BLOCKS(BS) \
+  (((RR_F32_CELL_WARPS * 32 + (BS) - 1) / (BS)) > 32 ? 32 : ((RR_F32_CELL_WARPS * 32 + (BS) - 1) / (BS)))
+
 __device__ __forceinline__ rrt::PT<float> p32_of(const Params& P) {
   rrt::PT<float> q;
   q.gamma = (float)P.gamma;
@@ -163,6 +175,7 @@ static __device__ __noinline__ void cell_item_f32(const StageArgs& a, int64_t c)
   }
   if (rc != ST_OK) {
     atomicCAS(a.b.st.status + q.i, 0, rc);
+    if (a.b.st.bad_cell) atomicMin(a.b.st.bad_cell + q.i, (long long)c);
     return;
   }
   store_cell(a, c, Un, Vn);
@@ -179,12 +192,12 @@ __global__ void __launch_bounds__(BS) k_faces_f32_persistent(StageArgs a) {
 }
 
 template <int BS, int PT>
-__global__ void __launch_bounds__(BS) k_cells_f32(StageArgs a) {
+__global__ void __launch_bounds__(BS, RR_F32_CELL_BLOCKS(BS)) k_cells_f32(StageArgs a) {
   grid_items<BS, PT>(a.b.c_end - a.b.c_begin, [&](int64_t t) { cell_item_f32(a, a.b.c_begin + t); });
 }
 
 template <int BS>
-__global__ void __launch_bounds__(BS) k_cells_f32_persistent(StageArgs a) {
+__global__ void __launch_bounds__(BS, RR_F32_CELL_BLOCKS(BS)) k_cells_f32_persistent(StageArgs a) {
   persistent_items(a.b.c_end - a.b.c_begin, a.work + 1,
                    [&](int64_t t) { cell_item_f32(a, a.b.c_begin + t); });
 }
@@ -272,6 +285,7 @@ __device__ __forceinline__ void fallback_cell_f32(const StageArgs& a, int64_t c,
     }
     if (rc != ST_OK) {
       atomicCAS(b.st.status + q.i, 0, rc);
+      if (b.st.bad_cell) atomicMin(b.st.bad_cell + q.i, (long long)c);
       return;
     }
     store_cell(a, c, Un, Vn);
