@@ -54,6 +54,7 @@ enum { RRMHD_RECON_GODUNOV = 0, RRMHD_RECON_MINMOD = 1, RRMHD_RECON_MC = 2, RRMH
 enum { RRMHD_BC_OUTFLOW = 0, RRMHD_BC_PERIODIC = 1 };
 enum { RRMHD_FP64 = 0, RRMHD_FP32_BULK = 1 };
 enum { RRMHD_SOLVER_PVM = 0, RRMHD_SOLVER_RADHLL = 1 };
+enum { RRMHD_CLOSURE_M1 = 0 };  /* the gray M1 closure, Eq. xi (Sec. 2.2) */
 
 /* One instance's grid.  Unused directions: n = 1, dx = 1.  bc applies to both
  * sides of a direction: outflow copies the edge cell into the two ghost layers
@@ -101,6 +102,8 @@ typedef struct {
                           divergence is kept to round-off.  In the FP32-bulk form the EMFs
                           are formed in FP64 from the FP32 fluxes.  0: cell-centred B
                           updated by its fluxes (default).                               */
+    int    closure;    /* the radiation closure: RRMHD_CLOSURE_M1 (Sec. 2.2, Eq. xi), the
+                          one the paper uses and the only one built (EINVAL otherwise)   */
 } rrmhd_opts;
 
 typedef struct rrmhd_ctx rrmhd_ctx;
@@ -169,6 +172,20 @@ rrmhd_status rrmhd_get_inst_status(const rrmhd_ctx* ctx, int32_t* status);
  * returns without synchronising. */
 rrmhd_status rrmhd_imex_step(rrmhd_ctx* ctx, int nsteps);
 
+/* One step as rrmhd_imex_step takes it, with every instance's dt capped:
+ * dt = min(cfl / max sum_d lambda_d/dx_d, dt_max), then clipped to t_end.  dt_max
+ * (> 0; +inf: no cap) applies to this call only.  dt_taken (host double[n_inst],
+ * may be NULL) receives each instance's dt (0 for an instance that did not step);
+ * with it the call synchronises the stream.  EINVAL for dt_max <= 0 or NaN. */
+rrmhd_status rrmhd_imex_step_dt(rrmhd_ctx* ctx, double dt_max, double* dt_taken);
+
+/* Per instance (host int64[n_inst]): the packed index of the lowest-numbered cell
+ * whose failure (no con2prim root, no implicit solution, after the admissibility
+ * fallback) froze the instance, or -1 if none did (also for an instance frozen by
+ * a NaN or non-positive time step, which no single cell causes).  Reset by
+ * rrmhd_set_state.  Synchronises the stream. */
+rrmhd_status rrmhd_get_first_bad_cell(const rrmhd_ctx* ctx, int64_t* cell);
+
 /* Same as rrmhd_imex_step, from and to HOST buffers: copies V_in (host
  * double[12][ncells], pinned memory recommended) to the device, takes nsteps steps
  * and copies the primitives back to V_out (host).  Synchronous.  If V_in equals
@@ -195,6 +212,17 @@ rrmhd_status rrmhd_con2prim(rrmhd_ctx* ctx, const double* U, const double* Zgues
  * approximation of |x| (Eq. iterat), A^2 products by nested flux differences.
  * Fhat: double[12][num_faces(dir)] laid out as rrmhd_face_offsets(dir). */
 rrmhd_status rrmhd_flux_sweep(rrmhd_ctx* ctx, int dir, double* Fhat);
+
+/* The flux sweep accumulated into a state (Eq. explicit, one direction): computes the
+ * numerical flux at every face normal to dir from the context's current primitives,
+ * as rrmhd_flux_sweep does, and updates U (double[12][ncells], the caller's, e.g. a
+ * copy of the context's U) in place:
+ *   U -= dt_weight / dx_dir (F^_{i+1/2} - F^_{i-1/2})
+ * at every cell of every instance (instances with fewer than dir+1 dimensions are
+ * left unchanged).  The FP64 form uses the FP64 operation order of the stage's flux
+ * difference; the FP32-bulk form differences its FP32 fluxes in FP32.  dt_weight >= 0.
+ * Uses the context's face buffer (not thread-safe against a concurrent step). */
+rrmhd_status rrmhd_flux_accumulate(rrmhd_ctx* ctx, int dir, double dt_weight, double* U);
 
 /* Implicit radiation-matter step of every cell (Sec. 3.3, Eqs. timeadv, totale,
  * totalm): solves E_r = E* - h G^0, F_r = F* - h G^i (Eqs. g0, gi) with

@@ -36,6 +36,9 @@ struct InstState {
   double* dt;
   unsigned long long* smax;  // max_cells sum_d lambda_d/dx_d, as the bits of a non-negative double
   int* status;               // 0 ok, else the first failing Status
+  const double* dt_max;      // [1] cap on every instance's dt (+inf: none), or null
+  long long* bad_cell;       // lowest index of a cell whose failure froze the instance
+                             // (LLONG_MAX: none), or null
 };
 
 struct Batch {
@@ -144,6 +147,13 @@ bool prepare_launch_shapes();
 bool prepare_launch_shapes_f64();
 bool prepare_launch_shapes_f32();
 void launch_begin_step(const Params& P, const Batch& b, cudaStream_t s);
+// U -= dt_weight / dx_dir (F_right - F_left) at every cell of the batch from the face
+// fluxes of direction dir (F64 stride fstride, or the FP32 ones when F32 is not null)
+void launch_flux_accumulate(const Batch& b, int dir, double dt_weight, const double* F64,
+                            const float* F32, int64_t fstride, int64_t out_base, double* U,
+                            cudaStream_t s);
+void launch_fill_i64(long long* p, int64_t n, long long v, cudaStream_t s);
+void launch_set_f64(double* p, double v, cudaStream_t s);
 void launch_end_step(const Batch& b, cudaStream_t s);
 void launch_prim2con_f64(const Params& P, const double* V, double* U, int64_t n, cudaStream_t s);
 void launch_con2prim_f64(const Params& P, const double* U, const double* Zg, double* V,

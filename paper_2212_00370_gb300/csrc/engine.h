@@ -42,7 +42,7 @@ inline bool opts_ok(const rrmhd_opts& o) {
          (o.precision == RRMHD_FP64 || o.precision == RRMHD_FP32_BULK) && o.lanes >= 1 &&
          (o.pvm_k == 3 || o.pvm_k == 4) && (o.pvm_products == 0 || o.pvm_products == 1) &&
          (o.solver == RRMHD_SOLVER_PVM || o.solver == RRMHD_SOLVER_RADHLL) &&
-         (o.ct == 0 || o.ct == 1);
+         (o.ct == 0 || o.ct == 1) && o.closure == RRMHD_CLOSURE_M1;
 }
 
 inline bool grid_ok(const rrmhd_grid& g, std::string& why) {
@@ -188,6 +188,8 @@ struct DeviceBufs {
   double *t = nullptr, *t_end = nullptr, *dt = nullptr;
   unsigned long long* smax = nullptr;
   int* status = nullptr;
+  double* dt_max = nullptr;        // [1] (contexts)
+  long long* bad_cell = nullptr;   // [n_inst] (contexts)
 };
 
 // Batch of instances [i0, i1) of a layout whose tables live in B.
@@ -207,6 +209,8 @@ inline Batch make_batch(const Layout& L, const DeviceBufs& B, int i0, int i1) {
   b.st.dt = B.dt;
   b.st.smax = B.smax;
   b.st.status = B.status;
+  b.st.dt_max = B.dt_max;
+  b.st.bad_cell = B.bad_cell;
   b.i_begin = i0;
   b.i_end = i1;
   b.c_begin = L.cell_off[i0];

@@ -160,6 +160,7 @@ void rrmhd_default_opts(rrmhd_opts* o) {
   o->pvm_products = 0;
   o->solver = RRMHD_SOLVER_PVM;
   o->ct = 0;
+  o->closure = RRMHD_CLOSURE_M1;
 }
 
 void rrmhd_destroy(rrmhd_ctx* c) {
@@ -175,7 +176,7 @@ void rrmhd_destroy(rrmhd_ctx* c) {
   void* bufs[] = {B.inst, B.cell_off, B.face_off, B.U0,  B.Ua,    B.Ub,   B.V0,
                   B.Va,   B.Vb,       B.kappa,    B.sigma, B.Fhat, B.t,    B.t_end,
                   B.dt,   B.smax,     B.status,   B.bad, B.jc,   B.edge_off, B.bf0,
-                  B.bfa,  B.bfb,      B.emf};
+                  B.bfa,  B.bfb,      B.emf,      B.dt_max, B.bad_cell};
   for (void* p : bufs)
     if (p) cudaFree(p);
   delete c;
@@ -225,6 +226,8 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
   A(dalloc(c, &B.dt, n_inst));
   A(dalloc(c, &B.smax, n_inst));
   A(dalloc(c, &B.status, n_inst));
+  A(dalloc(c, &B.dt_max, 1));
+  A(dalloc(c, &B.bad_cell, n_inst));
   A(dalloc(c, &B.bad, (size_t)L.ncells));
   A(dalloc(c, &B.jc, (size_t)17 * L.ncells));
   if (s == RRMHD_OK) {
@@ -251,6 +254,9 @@ rrmhd_status rrmhd_create(int n_inst, const rrmhd_grid* grids, const rrmhd_opts*
     A(cuda_check(c, cudaMemsetAsync(B.dt, 0, sizeof(double) * n_inst, st), "memset"));
     A(cuda_check(c, cudaMemsetAsync(B.smax, 0, sizeof(unsigned long long) * n_inst, st), "memset"));
     A(cuda_check(c, cudaMemsetAsync(B.status, 0, sizeof(int) * n_inst, st), "memset"));
+    rr::launch_set_f64(B.dt_max, std::numeric_limits<double>::infinity(), st);
+    rr::launch_fill_i64(B.bad_cell, n_inst, std::numeric_limits<long long>::max(), st);
+    A(cuda_check(c, cudaGetLastError(), "set-up kernels"));
     A(cuda_check(c, cudaMemsetAsync(B.kappa, 0, sizeof(double) * L.ncells, st), "memset"));
     A(cuda_check(c, cudaMemsetAsync(B.sigma, 0, sizeof(double) * L.ncells, st), "memset"));
     A(cuda_check(c, cudaMemsetAsync(B.U0, 0, sizeof(double) * N12, st), "memset"));
@@ -305,6 +311,7 @@ static rrmhd_status refresh_state(rrmhd_ctx* c) {
   rr::launch_prim2con_f64(c->P, cur_V(c), cur_U(c), c->L.ncells, c->stream);
   RR_CUDA(c, cudaMemsetAsync(c->B.smax, 0, sizeof(unsigned long long) * c->L.n_inst, c->stream));
   RR_CUDA(c, cudaMemsetAsync(c->B.status, 0, sizeof(int) * c->L.n_inst, c->stream));
+  rr::launch_fill_i64(c->B.bad_cell, c->L.n_inst, std::numeric_limits<long long>::max(), c->stream);
   RR_CUDA(c, cudaMemsetAsync(c->B.dt, 0, sizeof(double) * c->L.n_inst, c->stream));
   // a new state starts with an empty Jacobian cache (validity plane)
   RR_CUDA(c, cudaMemsetAsync(c->B.jc + (size_t)16 * c->L.ncells, 0, sizeof(double) * c->L.ncells, c->stream));
@@ -431,6 +438,28 @@ rrmhd_status rrmhd_imex_step(rrmhd_ctx* c, int nsteps) {
   return RRMHD_OK;
 }
 
+rrmhd_status rrmhd_imex_step_dt(rrmhd_ctx* c, double dt_max, double* dt_taken) {
+  if (!c || !(dt_max > 0.0)) return set_err(c, RRMHD_EINVAL, "bad argument");
+  rr::launch_set_f64(c->B.dt_max, dt_max, c->stream);
+  RR_CUDA(c, cudaGetLastError());
+  rrmhd_status s = rrmhd_imex_step(c, 1);
+  rr::launch_set_f64(c->B.dt_max, std::numeric_limits<double>::infinity(), c->stream);
+  RR_CUDA(c, cudaGetLastError());
+  if (s != RRMHD_OK) return s;
+  return dt_taken ? rrmhd_get_times(c, nullptr, dt_taken) : RRMHD_OK;
+}
+
+rrmhd_status rrmhd_get_first_bad_cell(const rrmhd_ctx* c, int64_t* cell) {
+  if (!c || !cell) return RRMHD_EINVAL;
+  std::vector<long long> h(c->L.n_inst);
+  RR_CUDA(c, cudaMemcpyAsync(h.data(), c->B.bad_cell, sizeof(long long) * c->L.n_inst,
+                             cudaMemcpyDeviceToHost, c->stream));
+  RR_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < c->L.n_inst; ++i)
+    cell[i] = h[i] == std::numeric_limits<long long>::max() ? -1 : (int64_t)h[i];
+  return RRMHD_OK;
+}
+
 rrmhd_status rrmhd_imex_step_host(rrmhd_ctx* c, const double* V_in, double* V_out, int nsteps) {
   if (!c || !V_in || !V_out || nsteps < 0) return set_err(c, RRMHD_EINVAL, "bad argument");
   const int64_t n = (int64_t)12 * c->L.ncells;
@@ -501,6 +530,37 @@ rrmhd_status rrmhd_flux_sweep(rrmhd_ctx* c, int dir, double* Fhat) {
     a.fstride = nd;
     a.out_base = c->L.dir_base[dir];
     rr::launch_faces_f64(a, c->tune.faces, c->stream);
+  }
+  RR_CUDA(c, cudaGetLastError());
+  return RRMHD_OK;
+}
+
+rrmhd_status rrmhd_flux_accumulate(rrmhd_ctx* c, int dir, double dt_weight, double* U) {
+  if (!c || !U || dir < 0 || dir > 2 || !(dt_weight >= 0.0))
+    return set_err(c, RRMHD_EINVAL, "bad argument");
+  Batch b = batch_of(c);
+  for (int d = 0; d < 3; ++d) b.f_count[d] = (d == dir) ? b.f_count[d] : 0;
+  StageArgs a = stage_args(c, b, 0, cur_U(c), cur_V(c), cur_U(c), cur_V(c), nullptr, nullptr);
+  a.check_active = 0;
+  a.work = batch_work(c)->work;
+  if (c->opts.ct) {
+    a.ct = 1;
+    a.fp32_fluxes = c->opts.precision == RRMHD_FP32_BULK;
+    a.bs = cur_b(c);
+  }
+  const int64_t nd = c->L.dir_base[dir + 1] - c->L.dir_base[dir];
+  if (c->opts.precision == RRMHD_FP32_BULK) {
+    // FP32 fluxes in the context's face buffer (columns = global face index)
+    rr::launch_faces_f32(a, c->tune.faces, c->stream);
+    rr::launch_flux_accumulate(batch_of(c), dir, dt_weight, nullptr, a.Fhat32, a.fstride, 0, U,
+                               c->stream);
+  } else {
+    a.Fhat = c->B.Fhat;
+    a.fstride = nd;
+    a.out_base = c->L.dir_base[dir];
+    rr::launch_faces_f64(a, c->tune.faces, c->stream);
+    rr::launch_flux_accumulate(batch_of(c), dir, dt_weight, c->B.Fhat, nullptr, nd,
+                               c->L.dir_base[dir], U, c->stream);
   }
   RR_CUDA(c, cudaGetLastError());
   return RRMHD_OK;

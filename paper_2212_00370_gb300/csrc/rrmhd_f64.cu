@@ -227,6 +227,7 @@ static __device__ __noinline__ void cell_item(const StageArgs& a, int64_t c) {
   }
   if (rc != ST_OK) {
     atomicCAS(a.b.st.status + q.i, 0, rc);
+    if (a.b.st.bad_cell) atomicMin(a.b.st.bad_cell + q.i, (long long)c);
     return;
   }
   store_cell(a, c, Un, Vn);
@@ -346,6 +347,7 @@ __device__ __forceinline__ void fallback_cell(const StageArgs& a, int64_t c, int
     }
     if (rc != ST_OK) {
       atomicCAS(b.st.status + q.i, 0, rc);
+      if (b.st.bad_cell) atomicMin(b.st.bad_cell + q.i, (long long)c);
       return;
     }
     store_cell(a, c, Un, Vn);
@@ -543,6 +545,7 @@ __global__ void k_begin_step(Params P, Batch b) {
   if (b.st.status[i] == 0 && t < te) {
     const double smax = __longlong_as_double((long long)b.st.smax[i]);
     dt = P.cfl / smax;
+    if (b.st.dt_max && dt > *b.st.dt_max) dt = *b.st.dt_max;
     if (t + dt > te) dt = te - t;
     if (!(dt > 0.0)) {  // NaN or non-positive speed bound
       dt = 0.0;
@@ -552,6 +555,49 @@ __global__ void k_begin_step(Params P, Batch b) {
   b.st.dt[i] = dt;
   b.st.smax[i] = 0ull;
 }
+
+// U -= (F_right - F_left) (dt_weight / dx_dir) at every cell (Eq. explicit, one
+// direction); the FP64 operation order of the stage's flux difference.  FP32 fluxes
+// (FP32-bulk) are differenced in FP32, as the FP32-bulk stage does.
+__global__ void k_flux_accumulate(Batch b, int dir, double dt_weight, const double* __restrict__ F64,
+                                  const float* __restrict__ F32, int64_t fstride, int64_t out_base,
+                                  double* U) {
+  const int64_t c = b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= b.c_end) return;
+  const CellPos q = cell_pos(b, c);
+  const InstDesc& I = q.I;
+  if (dir >= I.ndim) return;  // no faces normal to dir
+  const int m0 = I.n[0] + (dir == 0);
+  const int m1 = I.n[1] + (dir == 1);
+  const int64_t base = b.dir_base[dir] + b.face_off[(int64_t)dir * (b.n_inst + 1) + q.i];
+  int r[3] = {q.p[0], q.p[1], q.p[2]};
+  const int64_t fl = base + ((int64_t)r[2] * m1 + r[1]) * m0 + r[0] - out_base;
+  r[dir] += 1;
+  const int64_t fr = base + ((int64_t)r[2] * m1 + r[1]) * m0 + r[0] - out_base;
+  const int64_t N = b.ncells;
+  if (F32) {
+    const float dtdx = (float)(dt_weight / I.dx[dir]);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const float acc = (F32[k * fstride + fr] - F32[k * fstride + fl]) * dtdx;
+      U[k * N + c] = U[k * N + c] - (double)acc;
+    }
+  } else {
+    const double dtdx = dt_weight / I.dx[dir];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const double acc = (F64[k * fstride + fr] - F64[k * fstride + fl]) * dtdx;
+      U[k * N + c] = U[k * N + c] - acc;
+    }
+  }
+}
+
+__global__ void k_fill_i64(long long* p, int64_t n, long long v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+__global__ void k_set_f64(double* p, double v) { *p = v; }
 
 __global__ void k_end_step(Batch b) {
   const int i = b.i_begin + blockIdx.x * blockDim.x + threadIdx.x;
@@ -727,6 +773,19 @@ void launch_signal_f64(const Params& P, const Batch& b, const double* V, cudaStr
   if (n <= 0) return;
   k_signal<<<grid_for(n, 128), 128, 0, s>>>(P, b, V);
 }
+
+void launch_flux_accumulate(const Batch& b, int dir, double dt_weight, const double* F64,
+                            const float* F32, int64_t fstride, int64_t out_base, double* U,
+                            cudaStream_t s) {
+  const int64_t n = b.c_end - b.c_begin;
+  if (n > 0) k_flux_accumulate<<<grid_for(n, 128), 128, 0, s>>>(b, dir, dt_weight, F64, F32, fstride, out_base, U);
+}
+
+void launch_fill_i64(long long* p, int64_t n, long long v, cudaStream_t s) {
+  if (n > 0) k_fill_i64<<<grid_for(n, 256), 256, 0, s>>>(p, n, v);
+}
+
+void launch_set_f64(double* p, double v, cudaStream_t s) { k_set_f64<<<1, 1, 0, s>>>(p, v); }
 
 void launch_begin_step(const Params& P, const Batch& b, cudaStream_t s) {
   const int n = b.i_end - b.i_begin;

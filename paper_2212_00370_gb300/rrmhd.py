@@ -32,7 +32,8 @@ class rrmhd_opts(C.Structure):
                 ("pvm_eps", C.c_double), ("recon", C.c_int), ("beta_mode", C.c_int),
                 ("precision", C.c_int), ("c2p_maxit", C.c_int), ("imp_maxit", C.c_int),
                 ("imp_tol", C.c_double), ("lanes", C.c_int), ("pvm_k", C.c_int),
-                ("pvm_products", C.c_int), ("solver", C.c_int), ("ct", C.c_int)]
+                ("pvm_products", C.c_int), ("solver", C.c_int), ("ct", C.c_int),
+                ("closure", C.c_int)]
 
 
 class rrmhd_tuning(C.Structure):
@@ -96,10 +97,13 @@ _SIGNATURES = [
     ("rrmhd_get_times", C.c_int, [_VP, _DP, _DP]),
     ("rrmhd_get_inst_status", C.c_int, [_VP, _I32P]),
     ("rrmhd_imex_step", C.c_int, [_VP, C.c_int]),
+    ("rrmhd_imex_step_dt", C.c_int, [_VP, C.c_double, _DP]),
+    ("rrmhd_get_first_bad_cell", C.c_int, [_VP, C.POINTER(C.c_int64)]),
     ("rrmhd_imex_step_host", C.c_int, [_VP, _VP, _VP, C.c_int]),
     ("rrmhd_prim2con", C.c_int, [_VP, _VP, _VP, _I64]),
     ("rrmhd_con2prim", C.c_int, [_VP, _VP, _VP, _VP, _VP, _I64]),
     ("rrmhd_flux_sweep", C.c_int, [_VP, C.c_int, _VP]),
+    ("rrmhd_flux_accumulate", C.c_int, [_VP, C.c_int, C.c_double, _VP]),
     ("rrmhd_implicit_source", C.c_int, [_VP, C.c_double, _VP, _VP, _VP, _VP, _VP]),
     ("rrmhd_prim_z", C.c_int, [_VP, _VP, _VP, _I64]),
     ("rrmhd_profile_step", C.c_int, [_VP, _DP]),
@@ -312,6 +316,18 @@ class Context:
     def imex_step(self, nsteps=1):
         _check(self.ctx, lib().rrmhd_imex_step(self.ctx, int(nsteps)))
 
+    def imex_step_dt(self, dt_max):
+        """One step with every instance's dt capped at dt_max; returns the dt taken."""
+        dt = np.zeros(self.n_inst)
+        _check(self.ctx, lib().rrmhd_imex_step_dt(self.ctx, float(dt_max), dt.ctypes.data_as(_DP)))
+        return dt
+
+    def first_bad_cell(self):
+        """Per instance, the packed index of the lowest failing cell, or -1."""
+        cell = np.zeros(self.n_inst, dtype=np.int64)
+        _check(self.ctx, lib().rrmhd_get_first_bad_cell(self.ctx, cell.ctypes.data_as(C.POINTER(C.c_int64))))
+        return cell
+
     def imex_step_host(self, V_in, V_out, nsteps=1):
         """V_in, V_out: host float64 arrays [12][ncells] (pinned torch tensors or numpy)."""
         def hp(a):
@@ -347,6 +363,11 @@ class Context:
         F = self._t(12, self.num_faces(d))
         _check(self.ctx, lib().rrmhd_flux_sweep(self.ctx, d, _ptr(F)))
         return F
+
+    def flux_accumulate(self, d, dt_weight, U):
+        """U -= dt_weight/dx_d (F_right - F_left) in place (U: CUDA float64 [12][ncells])."""
+        _check(self.ctx, lib().rrmhd_flux_accumulate(self.ctx, int(d), float(dt_weight), _ptr(U)))
+        return U
 
     def implicit_source(self, hdt, Ustar, Zguess=None):
         U, V = self._t(12, self.ncells), self._t(12, self.ncells)

@@ -74,3 +74,15 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for f, _ in cls._fields_:
             assert int(got[name + "." + f]) == getattr(cls, f).offset, (name, f)
+
+
+def test_create_rejects_a_closure_other_than_m1(lib_path):
+    """Argument checks run before any CUDA call: no GPU needed."""
+    import ctypes as C
+    grid = rrmhd.make_grid(1, (8,), (0.125,))
+    opts = rrmhd.make_opts()
+    assert opts.closure == 0
+    opts.closure = 1
+    out = C.c_void_p()
+    rc = rrmhd.lib().rrmhd_create(1, C.byref(grid), C.byref(opts), None, C.byref(out))
+    assert rrmhd.STATUS[rc] == "EINVAL" and not out.value
