@@ -145,7 +145,7 @@ __device__ __forceinline__ int cell_update_f32(const StageArgs& a, int64_t c, co
   double jc[17];
 #pragma unroll
   for (int k = 0; k < 17; ++k) jc[k] = a.jc[k * N + c];
-  const int rc = implicit_cell<float>(a.P, a.kappa[c], a.sigma[c], cw * dt, Ust, prim_Z(a.P, vs), Un, Vn, jc);
+  const int rc = implicit_cell<FormBulk>(a.P, a.kappa[c], a.sigma[c], cw * dt, Ust, prim_Z(a.P, vs), Un, Vn, jc);
 #pragma unroll
   for (int k = 0; k < 17; ++k) a.jc[k * N + c] = jc[k];
   return rc;

@@ -223,6 +223,26 @@ struct ImpCell {
   double D, St[3], taut, B[3], Xs[4];
 };
 
+// Forms of the cell solver.  FormF64: the FP64 form, in the oracle's operation order
+// (bit parity).  FormBulk: the FP32-bulk form, whose faces carry FP32 rounding (~1e-7
+// relative), so its cells may spend less FP64 work where that changes no digit the
+// form keeps: the iteration matrix in FP32 (newton_dir), and the polish of the
+// converged root only where the radiation energy exceeds 100x the matter energy.  The
+// polish moves the root by ~1e-11 E_r; the matter (tau_e = tau_t - E_r, S = S_t - F_r)
+// takes that error relative to its own size, ~1e-11 E_r / tau_e: below 1e-9 unless the
+// radiation dominates, where it would reach the 1e-5 level (the 2D blast, E_r ~ 1e6
+// tau_e) and the polish is kept.
+struct FormF64 {
+  using Mat = double;
+  __device__ static bool polish(const ImpCell&, const double*) { return true; }
+};
+struct FormBulk {
+  using Mat = float;
+  __device__ static bool polish(const ImpCell& c, const double* X) {
+    return X[0] > 100.0 * (c.taut - X[0]);
+  }
+};
+
 __device__ __forceinline__ void matter_state(const ImpCell& c, const double* X, double* Um) {
   Um[0] = c.D;
   Um[1] = c.St[0] - X[1];
@@ -240,17 +260,17 @@ __device__ __forceinline__ void matter_state(const ImpCell& c, const double* X, 
 
 // Returns false if X is inadmissible (E_r <= 0 or no con2prim root).
 static __device__ __noinline__ bool imp_residual(const Params& P, const ImpCell& c, const double* X,
-                                          double Zg, double* R, double* V, double* Z) {
+                                                 double Zg, double* R, double* V, double* Z) {
   if (!(X[0] > 0.0)) return false;
   double Um[NV];
   matter_state(c, X, Um);
   if (con2prim(P, Um, Zg, V, Z) != ST_OK) return false;
   const double v2 = (V[1] * V[1] + V[2] * V[2]) + V[3] * V[3];
   const double W = 1.0 / sqrt(1.0 - v2);
-  const double u[3] = {W * V[1], W * V[2], W * V[3]};
   const double T = V[4] / V[0];
-  const double BP = P.a_rad * ((T * T) * (T * T));
   const M1 m = m1_coef(X[0], X[1], X[2], X[3]);
+  const double u[3] = {W * V[1], W * V[2], W * V[3]};
+  const double BP = P.a_rad * ((T * T) * (T * T));
   double Pr[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -337,8 +357,8 @@ __device__ __forceinline__ void picard_matrix(const ImpCell& c, const double* X,
 }
 
 // The iteration on X keeps its matrix J (an approximation of dR/dX: C^(m), the
-// cell's cache, Broyden updates, forward differences) in JT.  JT = double is the
-// FP64 form.  JT = float is the FP32-bulk form: the residual R, the iterate X and
+// cell's cache, Broyden updates, forward differences) in JT = F::Mat.  JT = double is
+// the FP64 form.  JT = float is the FP32-bulk form: the residual R, the iterate X and
 // every convergence test stay FP64, so the root is the FP64 root; only the Newton
 // direction is solved, and the matrix updated, in FP32.  A direction with a relative
 // error of ~1e-7 cond(J) is an inexact quasi-Newton step whose error the next FP64
@@ -381,9 +401,10 @@ __device__ __forceinline__ void broyden(JT J[4][4], const double* dXd, const dou
 
 // Forward-difference Jacobian of R at X (step 1e-7 E_r; a backward step where the
 // forward one leaves the admissible set).  False if neither is admissible.
-template <class JT>
+template <class F>
 static __device__ __noinline__ bool fd_jacobian(const Params& P, const ImpCell& c, const double* X,
-                                                const double* R, double Z, JT J[4][4]) {
+                                                const double* R, double Z, typename F::Mat J[4][4]) {
+  using JT = typename F::Mat;
   const double h = 1e-7 * X[0];
   for (int j = 0; j < 4; ++j) {
     double Xp[4] = {X[0], X[1], X[2], X[3]};
@@ -412,8 +433,8 @@ constexpr int IMP_POLISH_MAX = 6;         // at most six polishing corrections
 // halve the previous one means the rounding floor of R is reached: the polish stops
 // there without taking it.  last is the size of the converged step.  X, R, V and Z
 // stay those of the last accepted iterate.
-template <class JT>
-static __device__ __noinline__ void imp_polish(const Params& P, const ImpCell& c, JT J[4][4],
+template <class F>
+static __device__ __noinline__ void imp_polish(const Params& P, const ImpCell& c, typename F::Mat J[4][4],
                                                double* X, double* R, double* V, double* Z,
                                                double last) {
   double prev = last;
@@ -449,9 +470,10 @@ static __device__ __noinline__ void imp_polish(const Params& P, const ImpCell& c
 // halvings); converged
 // when the full step is <= imp_tol * E_r, then polished (imp_polish).  Returns true
 // on convergence.
-template <class JT>
+template <class F>
 static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c, double* X, double* R,
                                                double* V, double* Z, const double* Min, double* Mout) {
+  using JT = typename F::Mat;
   JT J[4][4];
   int need_fd = 0, fresh_fd = 0, first = 1;
   double prev = -1.0;
@@ -470,7 +492,7 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
   }
   for (int m = 1; m <= P.imp_maxit; ++m) {
     if (need_fd) {
-      if (!fd_jacobian(P, c, X, R, *Z, J)) return false;
+      if (!fd_jacobian<F>(P, c, X, R, *Z, J)) return false;
       need_fd = 0;
       fresh_fd = 1;
       first = 0;
@@ -505,7 +527,7 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           Mout[4 * i + j] = ((double)J[i][j] - (i == j ? 1.0 : 0.0)) / c.hdt;
-      imp_polish(P, c, J, X, R, V, Z, dfull);
+      if (F::polish(c, X)) imp_polish<F>(P, c, J, X, R, V, Z, dfull);
       return true;
     }
     const double r0 = ((R[0] * R[0] + R[1] * R[1]) + R[2] * R[2]) + R[3] * R[3];
@@ -693,7 +715,7 @@ __device__ __forceinline__ bool solve_matter(const Params& P, const ImpCell& c, 
 // last solve needed the matter primitives, and the next one starts there.  Order:
 // [flag 2: matter solve]; iteration on X; continuation in h on X; matter solve
 // (unless it was the first attempt).
-template <class JT = double>
+template <class F = FormF64>
 __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, double sigma,
                                              double hdt, const double* Us, double Zguess,
                                              double* U, double* V, double* jc = nullptr) {
@@ -735,7 +757,7 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
     Z = Zguess;
     imp_residual(P, c, X, Z, R, V, &Z);
   }
-  bool ok = imp_newton<JT>(P, c, X, R, V, &Z, (jc && jc[16] == 1.0) ? jc : nullptr, Mnew);
+  bool ok = imp_newton<F>(P, c, X, R, V, &Z, (jc && jc[16] == 1.0) ? jc : nullptr, Mnew);
   if (!ok) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) X[i] = c.Xs[i];
@@ -744,7 +766,7 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
     for (int j = IMP_LADDER; j >= 0 && ok; --j) {
       c.hdt = hdt / (double)(1 << j);
       ok = imp_residual(P, c, X, Z, R, V, &Z);
-      if (ok) ok = imp_newton<JT>(P, c, X, R, V, &Z, nullptr, Mnew);
+      if (ok) ok = imp_newton<F>(P, c, X, R, V, &Z, nullptr, Mnew);
     }
     c.hdt = hdt;
   }
