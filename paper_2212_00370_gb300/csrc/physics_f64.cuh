@@ -203,13 +203,14 @@ __device__ __forceinline__ void c2p_eval(const C2PIn& c, double x, C2PPt& e) {
   e.ok = 1;
 }
 
-// Returns a Status; V and *Zout are written only on success.
+// Returns a Status; V, *Zout and *Wout (the Lorentz factor; may be null) are written
+// only on success.
 // Stopping rule: the iteration stops at the Newton step with |dx| <= 1e-10 x (the
 // step is taken).  In Newton's quadratic regime the error left is of order
 // (1e-10 x)^2 / x, below rounding, so the PVM's finite-difference products, which
 // differentiate con2prim at the 1e-8 level, see a recovery exact to rounding.
 static __device__ __noinline__ int con2prim(const Params& P, const double* U, double Zguess,
-                                            double* V, double* Zout) {
+                                            double* V, double* Zout, double* Wout = nullptr) {
   C2PIn c;
   c.D = U[0];
   c.S[0] = U[1];
@@ -264,6 +265,7 @@ static __device__ __noinline__ int con2prim(const Params& P, const double* U, do
 #pragma unroll
   for (int k = 5; k < NV; ++k) V[k] = U[k];
   if (Zout) *Zout = e.Z;
+  if (Wout) *Wout = e.W;
   return ST_OK;
 }
 

@@ -221,23 +221,28 @@ __device__ __forceinline__ void llf_flux(const Params& P, int d, const double* V
 struct ImpCell {
   double kappa, sigma, hdt;
   double D, St[3], taut, B[3], Xs[4];
+  double iD;  // 1/D (the FP32-bulk form's residual)
 };
 
 // Forms of the cell solver.  FormF64: the FP64 form, in the oracle's operation order
 // (bit parity).  FormBulk: the FP32-bulk form, whose faces carry FP32 rounding (~1e-7
 // relative), so its cells may spend less FP64 work where that changes no digit the
-// form keeps: the iteration matrix in FP32 (newton_dir), and the polish of the
-// converged root only where the radiation energy exceeds 100x the matter energy.  The
+// form keeps: the iteration matrix in FP32 (newton_dir); a residual that takes W from
+// con2prim's root and T = p W / D (a square root and two divisions fewer, the same
+// values to rounding); and the polish of the converged root only where the radiation
+// energy exceeds 100x the matter energy.  The
 // polish moves the root by ~1e-11 E_r; the matter (tau_e = tau_t - E_r, S = S_t - F_r)
 // takes that error relative to its own size, ~1e-11 E_r / tau_e: below 1e-9 unless the
 // radiation dominates, where it would reach the 1e-5 level (the 2D blast, E_r ~ 1e6
 // tau_e) and the polish is kept.
 struct FormF64 {
   using Mat = double;
+  static constexpr bool kReuseW = false;
   __device__ static bool polish(const ImpCell&, const double*) { return true; }
 };
 struct FormBulk {
   using Mat = float;
+  static constexpr bool kReuseW = true;
   __device__ static bool polish(const ImpCell& c, const double* X) {
     return X[0] > 100.0 * (c.taut - X[0]);
   }
@@ -259,15 +264,22 @@ __device__ __forceinline__ void matter_state(const ImpCell& c, const double* X, 
 }
 
 // Returns false if X is inadmissible (E_r <= 0 or no con2prim root).
+template <class F>
 static __device__ __noinline__ bool imp_residual(const Params& P, const ImpCell& c, const double* X,
                                                  double Zg, double* R, double* V, double* Z) {
   if (!(X[0] > 0.0)) return false;
   double Um[NV];
   matter_state(c, X, Um);
-  if (con2prim(P, Um, Zg, V, Z) != ST_OK) return false;
-  const double v2 = (V[1] * V[1] + V[2] * V[2]) + V[3] * V[3];
-  const double W = 1.0 / sqrt(1.0 - v2);
-  const double T = V[4] / V[0];
+  double W, T;
+  if constexpr (F::kReuseW) {  // W of con2prim's root; T = p / rho = p W / D
+    if (con2prim(P, Um, Zg, V, Z, &W) != ST_OK) return false;
+    T = V[4] * (W * c.iD);
+  } else {
+    if (con2prim(P, Um, Zg, V, Z) != ST_OK) return false;
+    const double v2 = (V[1] * V[1] + V[2] * V[2]) + V[3] * V[3];
+    W = 1.0 / sqrt(1.0 - v2);
+    T = V[4] / V[0];
+  }
   const M1 m = m1_coef(X[0], X[1], X[2], X[3]);
   const double u[3] = {W * V[1], W * V[2], W * V[3]};
   const double BP = P.a_rad * ((T * T) * (T * T));
@@ -410,9 +422,9 @@ static __device__ __noinline__ bool fd_jacobian(const Params& P, const ImpCell& 
     double Xp[4] = {X[0], X[1], X[2], X[3]};
     double Rp[4], Vp[NV], Zp;
     Xp[j] = X[j] + h;
-    if (!imp_residual(P, c, Xp, Z, Rp, Vp, &Zp)) {
+    if (!imp_residual<F>(P, c, Xp, Z, Rp, Vp, &Zp)) {
       Xp[j] = X[j] - h;
-      if (!imp_residual(P, c, Xp, Z, Rp, Vp, &Zp)) return false;
+      if (!imp_residual<F>(P, c, Xp, Z, Rp, Vp, &Zp)) return false;
     }
     const double dXj = Xp[j] - X[j];
 #pragma unroll
@@ -449,7 +461,7 @@ static __device__ __noinline__ void imp_polish(const Params& P, const ImpCell& c
     double Xn[4], Rn[4], Vn[NV], Zn = *Z;
 #pragma unroll
     for (int i = 0; i < 4; ++i) Xn[i] = X[i] + dX[i];
-    if (!imp_residual(P, c, Xn, *Z, Rn, Vn, &Zn)) return;
+    if (!imp_residual<F>(P, c, Xn, *Z, Rn, Vn, &Zn)) return;
     broyden(J, dX, R, Rn);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -513,7 +525,7 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
     if (dfull <= P.imp_tol * X[0]) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) Xn[i] = X[i] + dX[i];
-      if (!imp_residual(P, c, Xn, *Z, Rn, Vn, &Zn)) return false;
+      if (!imp_residual<F>(P, c, Xn, *Z, Rn, Vn, &Zn)) return false;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         X[i] = Xn[i];
@@ -536,7 +548,7 @@ static __device__ __noinline__ bool imp_newton(const Params& P, const ImpCell& c
     for (int k = 0; k < 10; ++k) {  // at most ten halvings
 #pragma unroll
       for (int i = 0; i < 4; ++i) Xn[i] = X[i] + dX[i];
-      if (imp_residual(P, c, Xn, *Z, Rn, Vn, &Zn)) {
+      if (imp_residual<F>(P, c, Xn, *Z, Rn, Vn, &Zn)) {
         const double r1 = ((Rn[0] * Rn[0] + Rn[1] * Rn[1]) + Rn[2] * Rn[2]) + Rn[3] * Rn[3];
         if (r1 <= (1.0 - 1e-4 * lam) * r0) {
           ok = 1;
@@ -740,7 +752,8 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
   double X[4] = {c.Xs[0], c.Xs[1], c.Xs[2], c.Xs[3]};
   double R[4], Z = Zguess;
   // no admissible matter state at X*: the explicit update U* itself is inadmissible
-  if (!imp_residual(P, c, X, Zguess, R, V, &Z)) return ST_C2P;
+  if constexpr (F::kReuseW) c.iD = 1.0 / c.D;
+  if (!imp_residual<F>(P, c, X, Zguess, R, V, &Z)) return ST_C2P;
   double Mnew[16], Vs[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) Vs[k] = V[k];
@@ -755,7 +768,7 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
 #pragma unroll
     for (int k = 0; k < NV; ++k) V[k] = Vs[k];
     Z = Zguess;
-    imp_residual(P, c, X, Z, R, V, &Z);
+    imp_residual<F>(P, c, X, Z, R, V, &Z);
   }
   bool ok = imp_newton<F>(P, c, X, R, V, &Z, (jc && jc[16] == 1.0) ? jc : nullptr, Mnew);
   if (!ok) {
@@ -765,7 +778,7 @@ __device__ __forceinline__ int implicit_cell(const Params& P, double kappa, doub
     ok = true;
     for (int j = IMP_LADDER; j >= 0 && ok; --j) {
       c.hdt = hdt / (double)(1 << j);
-      ok = imp_residual(P, c, X, Z, R, V, &Z);
+      ok = imp_residual<F>(P, c, X, Z, R, V, &Z);
       if (ok) ok = imp_newton<F>(P, c, X, R, V, &Z, nullptr, Mnew);
     }
     c.hdt = hdt;
