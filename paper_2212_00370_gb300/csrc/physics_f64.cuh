@@ -173,19 +173,33 @@ struct C2PPt {
   double x, Z, iZ, iZB, v2, W, p, f, df;
 };
 
+// FAST (the FP32-bulk form's cells): 1/Z and 1/(Z+B^2) from one division, W from
+// rsqrt; the same values to a few ulps.  Otherwise the operation order above.
+template <bool FAST = false>
 __device__ __forceinline__ void c2p_eval(const C2PIn& c, double x, C2PPt& e) {
   e.x = x;
   e.ok = 0;
   if (!(x > 0.0)) return;
   const double Z = x + c.D;
   const double ZB = Z + c.B2;
-  const double iZ = 1.0 / Z;
-  const double iZB = 1.0 / ZB;
+  double iZ, iZB;
+  if constexpr (FAST) {
+    const double q = 1.0 / (Z * ZB);
+    iZ = ZB * q;
+    iZB = Z * q;
+  } else {
+    iZ = 1.0 / Z;
+    iZB = 1.0 / ZB;
+  }
   const double iZ2 = iZ * iZ;
   const double v2 = (c.S2 + c.SB2 * ((2.0 * Z + c.B2) * iZ2)) * (iZB * iZB);
   if (!(v2 < 1.0)) return;
   const double omv2 = 1.0 - v2;
-  const double W = 1.0 / sqrt(omv2);
+  double W;
+  if constexpr (FAST)
+    W = rsqrt(omv2);
+  else
+    W = 1.0 / sqrt(omv2);
   const double p = c.gm1g * (x * omv2 - c.D * (v2 / (W + 1.0)));
   const double f = ((x - p) + (0.5 * c.B2) * (1.0 + v2)) - ((0.5 * c.SB2) * iZ2 + c.tau);
   const double dv2 = (-2.0 * ((iZB * iZB) * iZB)) *
@@ -209,6 +223,7 @@ __device__ __forceinline__ void c2p_eval(const C2PIn& c, double x, C2PPt& e) {
 // step is taken).  In Newton's quadratic regime the error left is of order
 // (1e-10 x)^2 / x, below rounding, so the PVM's finite-difference products, which
 // differentiate con2prim at the 1e-8 level, see a recovery exact to rounding.
+template <bool FAST = false>
 static __device__ __noinline__ int con2prim(const Params& P, const double* U, double Zguess,
                                             double* V, double* Zout, double* Wout = nullptr) {
   C2PIn c;
@@ -230,10 +245,10 @@ static __device__ __noinline__ int con2prim(const Params& P, const double* U, do
   double x = Zguess - c.D;
   if (!(x > 0.0)) x = (c.tau > 0.0) ? c.tau : c.D;
   C2PPt e;
-  c2p_eval(c, x, e);
+  c2p_eval<FAST>(c, x, e);
   for (int k = 0; k < 200 && !e.ok; ++k) {
     x = 2.0 * x;
-    c2p_eval(c, x, e);
+    c2p_eval<FAST>(c, x, e);
   }
   if (!e.ok) return ST_C2P;
 
@@ -241,10 +256,10 @@ static __device__ __noinline__ int con2prim(const Params& P, const double* U, do
   for (int it = 1; it <= P.c2p_maxit; ++it) {
     double dx = -e.f / e.df;
     C2PPt en;
-    c2p_eval(c, x + dx, en);
+    c2p_eval<FAST>(c, x + dx, en);
     for (int k = 0; k < 60 && !en.ok; ++k) {
       dx = 0.5 * dx;
-      c2p_eval(c, x + dx, en);
+      c2p_eval<FAST>(c, x + dx, en);
     }
     if (!en.ok) break;
     x = en.x;

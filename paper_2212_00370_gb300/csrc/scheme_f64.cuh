@@ -229,8 +229,9 @@ struct ImpCell {
 // relative), so its cells may spend less FP64 work where that changes no digit the
 // form keeps: the iteration matrix in FP32 (newton_dir); a residual that takes W from
 // con2prim's root and T = p W / D (a square root and two divisions fewer, the same
-// values to rounding); and the polish of the converged root only where the radiation
-// energy exceeds 100x the matter energy.  The
+// values to rounding); con2prim evaluations with 1/Z and 1/(Z+B^2) from one division
+// and W from rsqrt (c2p_eval<true>, the same values to a few ulps); and the polish of
+// the converged root only where the radiation energy exceeds 100x the matter energy.  The
 // polish moves the root by ~1e-11 E_r; the matter (tau_e = tau_t - E_r, S = S_t - F_r)
 // takes that error relative to its own size, ~1e-11 E_r / tau_e: below 1e-9 unless the
 // radiation dominates, where it would reach the 1e-5 level (the 2D blast, E_r ~ 1e6
@@ -238,11 +239,13 @@ struct ImpCell {
 struct FormF64 {
   using Mat = double;
   static constexpr bool kReuseW = false;
+  static constexpr bool kFastC2P = false;
   __device__ static bool polish(const ImpCell&, const double*) { return true; }
 };
 struct FormBulk {
   using Mat = float;
   static constexpr bool kReuseW = true;
+  static constexpr bool kFastC2P = true;
   __device__ static bool polish(const ImpCell& c, const double* X) {
     return X[0] > 100.0 * (c.taut - X[0]);
   }
@@ -272,7 +275,7 @@ static __device__ __noinline__ bool imp_residual(const Params& P, const ImpCell&
   matter_state(c, X, Um);
   double W, T;
   if constexpr (F::kReuseW) {  // W of con2prim's root; T = p / rho = p W / D
-    if (con2prim(P, Um, Zg, V, Z, &W) != ST_OK) return false;
+    if (con2prim<F::kFastC2P>(P, Um, Zg, V, Z, &W) != ST_OK) return false;
     T = V[4] * (W * c.iD);
   } else {
     if (con2prim(P, Um, Zg, V, Z) != ST_OK) return false;
