@@ -254,7 +254,14 @@ static __device__ __noinline__ int con2prim(const Params& P, const double* U, do
 
   int conv = 0;
   for (int it = 1; it <= P.c2p_maxit; ++it) {
-    double dx = -e.f / e.df;
+    double dx;
+    if constexpr (FAST) {  // inexact Newton: an FP32 reciprocal of df (~6e-8 relative)
+      const float d32 = (float)e.df;
+      dx = (fabsf(d32) > 1e-30f && fabsf(d32) < 1e30f) ? -e.f * (double)__frcp_rn(d32)
+                                                        : -e.f / e.df;
+    } else {
+      dx = -e.f / e.df;
+    }
     C2PPt en;
     c2p_eval<FAST>(c, x + dx, en);
     for (int k = 0; k < 60 && !en.ok; ++k) {
@@ -270,7 +277,7 @@ static __device__ __noinline__ int con2prim(const Params& P, const double* U, do
     }
   }
   if (!conv || !(e.p > 0.0)) return ST_C2P;
-  const double rho = c.D / e.W;
+  const double rho = FAST ? c.D * ((1.0 - e.v2) * e.W) : c.D / e.W;  // D/W = D (1 - v^2) W
   const double SBiZ = c.SB * e.iZ;
   V[0] = rho;
   V[1] = (c.S[0] + SBiZ * c.B[0]) * e.iZB;

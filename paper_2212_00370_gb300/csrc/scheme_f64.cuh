@@ -229,9 +229,10 @@ struct ImpCell {
 // relative), so its cells may spend less FP64 work where that changes no digit the
 // form keeps: the iteration matrix in FP32 (newton_dir); a residual that takes W from
 // con2prim's root and T = p W / D (a square root and two divisions fewer, the same
-// values to rounding); con2prim evaluations with 1/Z and 1/(Z+B^2) from one division
-// and W from rsqrt (c2p_eval<true>, the same values to a few ulps); and the polish of
-// the converged root only where the radiation energy exceeds 100x the matter energy.  The
+// values to rounding); con2prim<true>: evaluations with 1/Z and 1/(Z+B^2) from one
+// division and W from rsqrt, Newton steps with an FP32 reciprocal of the derivative,
+// rho = D (1 - v^2) W (the same root to a few ulps); and the polish of the converged
+// root only where the radiation energy exceeds 100x the matter energy.  The
 // polish moves the root by ~1e-11 E_r; the matter (tau_e = tau_t - E_r, S = S_t - F_r)
 // takes that error relative to its own size, ~1e-11 E_r / tau_e: below 1e-9 unless the
 // radiation dominates, where it would reach the 1e-5 level (the 2D blast, E_r ~ 1e6
