@@ -96,6 +96,9 @@ def parse():
                    help="instances in the CPU sample (default: 1024 for the cpu_baseline leg, "
                         "the whole batch for --impl reference)")
     p.add_argument("--lanes", type=int, default=8, help="independent sub-batches (streams)")
+    p.add_argument("--recon", default="vanleer", choices=["vanleer", "minmod", "mc", "godunov"],
+                   help="reconstruction of the timed C1 lines (Sec. 3.2); godunov times the "
+                        "path without PLM, whose cost it isolates")
     p.add_argument("--precision", default="both", choices=["both", "fp64", "fp32_bulk", "fp64_tangent"],
                    help="both: FP32-bulk is the headline value, FP64 (and FP64 with tangent "
                         "products) reported beside it")
@@ -265,6 +268,7 @@ def measure(a, precision, rank, world, local, peaks):
     w = W.riemann_batch(a.instances, seed=seed)
     grids = [rrmhd.make_grid(1, g["n"], g["dx"], g["bc"]) for g in w.grids]
     extra = {"pvm_products": 1} if precision == "fp64_tangent" else {}
+    extra["recon"] = a.recon
     ctx = rrmhd.Context(grids, gamma=w.gamma, a_rad=w.a_rad, cfl=w.cfl, lanes=a.lanes,
                         precision="fp64" if precision == "fp64_tangent" else precision, **extra)
     ctx.set_opacity(torch.tensor(w.kappa, device="cuda"), torch.tensor(w.sigma, device="cuda"))
@@ -639,9 +643,10 @@ DTYPE = {"fp64": "f64", "fp32_bulk": "f32 faces + f64 cells", "fp64_tangent": "f
 METRIC = "zone-updates/s per IMEX step (FP32-bulk vs FP64, 1 GB300; % of roofline; p50/p99 step time)"
 
 
-def workload_name(n_inst):
+def workload_name(n_inst, recon="vanleer"):
+    names = {"vanleer": "VanLeer", "minmod": "MinMod", "mc": "MC", "godunov": "first order"}
     return ("C1: %d independent 1D RRMHD Riemann problems per GPU, N~U{128..2048}, seed "
-            "2212003701+rank, gamma 4/3, PVM-int-8 + VanLeer + IMEX-RK3" % n_inst)
+            "2212003701+rank, gamma 4/3, PVM-int-8 + %s + IMEX-RK3" % (n_inst, names[recon]))
 
 
 def run_c0(a):
@@ -678,7 +683,7 @@ def run_ours(a, rank, world, pool, cores):
         "value": head["value"], "unit": "zone-updates/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[precisions[0]], "data": "synthetic",
-        "config": {"workload": workload_name(a.instances), "precision": precisions[0],
+        "config": {"workload": workload_name(a.instances, a.recon), "precision": precisions[0],
                    "instances": a.instances, "cells": head["cells"],
                    "live_instances": head["live"], "failed_instances": head["failed"],
                    "parallelism": "replicas (independent problems per GPU); %d lanes (streams) per GPU"

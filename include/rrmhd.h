@@ -73,7 +73,10 @@ typedef struct {
     double cfl;        /* Courant number of dt = cfl / max sum_d lambda_d/dx_d            */
     double pvm_eps;    /* epsilon of the nested flux differences, Sec. 3.2.2 (1e-8)        */
     int    recon;      /* RRMHD_RECON_* (Sec. 3.2); VanLeer is the paper's default         */
-    int    beta_mode;  /* 1: beta = min(1/tau_L, 1/tau_R, 1) (Eq. beta); 0: beta = 1        */
+    int    beta_mode;  /* 1: beta = min(1/tau_L, 1/tau_R, 1) (Eq. beta); 0: beta = 1;
+                          2: Eq. beta on the radiation components (E_r, F_r) of the PVM
+                          viscosity and beta = 1 on the magnetofluid ones (a variant: the
+                          paper leaves other choices of beta open, Sec. 5)             */
     int    precision;  /* RRMHD_FP64 (reproducible) or RRMHD_FP32_BULK                     */
     int    c2p_maxit;  /* Newton iterations allowed in con2prim (60)                       */
     int    imp_maxit;  /* iterations allowed in one implicit Newton solve (50)             */
@@ -94,7 +97,7 @@ typedef struct {
                           radiative HLL of Sec. 3.2.1, HLL per block with the fast-
                           magnetosonic speeds for the magnetofluid and lambda_r1/lambda_r3
                           (Eqs. lam1-lam3) for the radiation, the latter capped at
-                          4/(3 tau) (Eq. limits) when beta_mode = 1                      */
+                          4/(3 tau) (Eq. limits) when beta_mode = 1 or 2                 */
     int    ct;         /* 1: constrained transport of the magnetic field on 2D/3D instances
                           (CT-contact EMFs of Gardiner & Stone 2005, the scheme the paper's
                           multi-D runs use, Sec. 4): the normal field lives on the faces,

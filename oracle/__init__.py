@@ -59,7 +59,7 @@ class Params:
     cfl: float = 0.4
     pvm_eps: float = 1e-8
     recon: str = "vanleer"
-    beta: bool = True
+    beta: object = True     # True: Eq. beta; False: beta = 1; "radiation": Eq. beta on E_r, F_r only
     implicit: str = "newton"
     c2p_maxit: int = 60
     imp_maxit: int = 50
@@ -69,7 +69,8 @@ class Params:
 
     def struct(self):
         p = _Params(self.gamma, self.a_rad, self.cfl, self.pvm_eps, RECON[self.recon],
-                    1 if self.beta else 0, {"newton": 0, "picard": 1, "matter": 2}[self.implicit], self.pvm_k,
+                    2 if self.beta == "radiation" else (1 if self.beta else 0),
+                    {"newton": 0, "picard": 1, "matter": 2}[self.implicit], self.pvm_k,
                     {"pvm": 0, "radhll": 1}[self.solver],
                     self.c2p_maxit, self.imp_maxit, self.imp_tol, 0.0, 0.0)
         lib().or_params_init(C.byref(p))

@@ -48,7 +48,8 @@ typedef struct {
     double cfl;        /* Courant number                                           */
     double pvm_eps;    /* epsilon of the nested flux differences (Sec. 3.2.2, 1e-8) */
     int    recon;      /* OR_RECON_*                                               */
-    int    beta_mode;  /* 1: beta = min(1/tau_L, 1/tau_R, 1) (Eq. beta); 0: beta=1  */
+    int    beta_mode;  /* 1: beta = min(1/tau_L, 1/tau_R, 1) (Eq. beta); 0: beta=1;
+                          2: Eq. beta on the radiation components, 1 on the others   */
     int    imp_mode;   /* OR_IMP_NEWTON (default), OR_IMP_PICARD (paper's C matrix), or
                           OR_IMP_MATTER (the matter-primitive iteration alone) */
     int    pvm_k;      /* PVM-int-n with n = 2^k (Eq. iterat): 3 (PVM-int-8), 4 (-16) */

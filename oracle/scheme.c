@@ -121,7 +121,9 @@ static int a2_product(pvm_ctx* c, const double w[12], double out[12])
  * k = 3 (PVM-int-8) is the paper's solver: four products, U_4 = U_{k+1}.  k = 4
  * (PVM-int-16) is the variant the paper reports testing.
  * and beta = min{1/tau_L, 1/tau_R, 1} (Eq. beta), tau = rho W (kappa + sigma) dx
- * at the two cell centres adjacent to the face.
+ * at the two cell centres adjacent to the face (beta_mode 1), applied to the radiation
+ * components only (beta_mode 2, a variant: the paper leaves other choices of beta
+ * open), or beta = 1 (beta_mode 0).
  * If a con2prim inside the viscosity term fails, the face uses Q = I
  * (U_{k+1} = U_0, the lambda_max = 1 Rusanov flux) and returns 1. */
 int or_pvm_flux(const or_params* P, int dir, const double VL[12], const double VR[12],
@@ -172,7 +174,12 @@ int or_pvm_flux(const or_params* P, int dir, const double VL[12], const double V
         for (int k = 0; k < 12; k++) Ul[k] = U0[k];
         if (st) st->pvm_fallback++;
     }
-    for (int k = 0; k < 12; k++) Fhat[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * (beta * Ul[k]);
+    /* beta_mode 2: beta damps the radiation block (E_r, F_r) only; the magnetofluid
+     * block keeps beta = 1 */
+    for (int k = 0; k < 12; k++) {
+        double bk = (P->beta_mode == 2 && k < 8) ? 1.0 : beta;
+        Fhat[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * (bk * Ul[k]);
+    }
     if (U4out)
         for (int k = 0; k < 12; k++) U4out[k] = Ul[k];
     return fail;

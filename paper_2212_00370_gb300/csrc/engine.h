@@ -38,6 +38,7 @@ inline Params make_params(const rrmhd_opts& o) {
 
 inline bool opts_ok(const rrmhd_opts& o) {
   return o.gamma > 1.0 && o.a_rad >= 0.0 && o.cfl > 0.0 && o.pvm_eps > 0.0 && o.recon >= 0 &&
+         o.beta_mode >= 0 && o.beta_mode <= 2 &&
          o.recon <= 3 && o.c2p_maxit >= 1 && o.imp_maxit >= 1 && o.imp_tol > 0.0 &&
          (o.precision == RRMHD_FP64 || o.precision == RRMHD_FP32_BULK) && o.lanes >= 1 &&
          (o.pvm_k == 3 || o.pvm_k == 4) && (o.pvm_products == 0 || o.pvm_products == 1) &&

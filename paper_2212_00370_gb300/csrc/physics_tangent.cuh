@@ -402,7 +402,8 @@ __device__ __forceinline__ int pvm_flux(const PT<S>& P, int d, const S* VL, cons
     for (int k = 0; k < NV; ++k) Ul[k] = U0[k];
   }
 #pragma unroll
-  for (int k = 0; k < NV; ++k) Fhat[k] -= S(0.5) * (beta * Ul[k]);
+  for (int k = 0; k < NV; ++k)
+    Fhat[k] -= S(0.5) * (((P.beta_mode == 2 && k < 8) ? S(1) : beta) * Ul[k]);  // 2: radiation only
   return fail;
 }
 

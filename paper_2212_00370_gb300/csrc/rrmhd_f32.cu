@@ -30,9 +30,16 @@ constexpr int kCellThreads = 128;
 #ifndef RR_F32_CELL_WARPS
 #define RR_F32_CELL_WARPS 12
 #endif
-// (at most 32 resident blocks per SM: partial-warp blocks of 8 threads keep no bound)
-#define RR_F32_CELL_BLOCKS(BS) \
-  (((RR_F32_CELL_WARPS * 32 + (BS) - 1) / (BS)) > 32 ? 32 : ((RR_F32_CELL_WARPS * 32 + (BS) - 1) / (BS)))
+// Blocks per SM for a warp target W (at most 32 resident blocks per SM: partial-warp
+// blocks of 8 threads keep no bound).
+#define RR_F32_BLOCKS(W, BS) ((((W) * 32 + (BS) - 1) / (BS)) > 32 ? 32 : (((W) * 32 + (BS) - 1) / (BS)))
+#define RR_F32_CELL_BLOCKS(BS) RR_F32_BLOCKS(RR_F32_CELL_WARPS, BS)
+// The FP32 face kernels (127 registers unbounded) at 24 warps per SM (85 registers):
+// 8 % shorter face launches.
+#ifndef RR_F32_FACE_WARPS
+#define RR_F32_FACE_WARPS 24
+#endif
+#define RR_F32_FACE_BLOCKS(BS) RR_F32_BLOCKS(RR_F32_FACE_WARPS, BS)
 
 __device__ __forceinline__ rrt::PT<float> p32_of(const Params& P) {
   rrt::PT<float> q;
@@ -182,12 +189,12 @@ static __device__ __noinline__ void cell_item_f32(const StageArgs& a, int64_t c)
 }
 
 template <int BS, int PT>
-__global__ void __launch_bounds__(BS) k_faces_f32(StageArgs a) {
+__global__ void __launch_bounds__(BS, RR_F32_FACE_BLOCKS(BS)) k_faces_f32(StageArgs a) {
   grid_items<BS, PT>(lane_faces(a.b), [&](int64_t t) { face_item_f32(a, t); });
 }
 
 template <int BS>
-__global__ void __launch_bounds__(BS) k_faces_f32_persistent(StageArgs a) {
+__global__ void __launch_bounds__(BS, RR_F32_FACE_BLOCKS(BS)) k_faces_f32_persistent(StageArgs a) {
   persistent_items(lane_faces(a.b), a.work, [&](int64_t t) { face_item_f32(a, t); });
 }
 

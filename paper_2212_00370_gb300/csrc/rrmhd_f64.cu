@@ -90,7 +90,10 @@ __device__ __forceinline__ int pvm_flux_tangent(const Params& P, int d, const do
     for (int k = 0; k < NV; ++k) Ul[k] = U0[k];
   }
 #pragma unroll
-  for (int k = 0; k < NV; ++k) Fhat[k] = Fhat[k] - 0.5 * (beta * Ul[k]);
+  for (int k = 0; k < NV; ++k) {
+    const double bk = (P.beta_mode == 2 && k < 8) ? 1.0 : beta;  // beta_mode 2: radiation only
+    Fhat[k] = Fhat[k] - 0.5 * (bk * Ul[k]);
+  }
   return fail;
 }
 

@@ -149,8 +149,12 @@ __device__ __forceinline__ int pvm_flux(const Params& P, int d, const double* VL
 #pragma unroll
     for (int k = 0; k < NV; ++k) Ul[k] = U0[k];
   }
+  // beta_mode 2: Eq. beta on the radiation block only (beta = 1 on the magnetofluid)
 #pragma unroll
-  for (int k = 0; k < NV; ++k) Fhat[k] = Fhat[k] - 0.5 * (beta * Ul[k]);
+  for (int k = 0; k < NV; ++k) {
+    const double bk = (P.beta_mode == 2 && k < 8) ? 1.0 : beta;
+    Fhat[k] = Fhat[k] - 0.5 * (bk * Ul[k]);
+  }
   return fail;
 }
 

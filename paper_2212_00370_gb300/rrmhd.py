@@ -182,7 +182,7 @@ def make_opts(**kw):
         if k == "precision" and isinstance(v, str):
             v = PRECISION[v]
         if k == "beta":
-            k, v = "beta_mode", int(bool(v))
+            k, v = "beta_mode", (2 if v == "radiation" else int(bool(v)))
         if k == "pvm_products" and isinstance(v, str):
             v = {"fd": 0, "tangent": 1}[v]
         if k == "solver" and isinstance(v, str):

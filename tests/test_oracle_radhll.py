@@ -213,6 +213,17 @@ def test_pulse_follows_the_diffusion_solution(sigma):
     assert e["pvm"] < e["radhll"]
 
 
+def test_pulse_with_radiation_only_beta():
+    """beta on the radiation block alone (beta_mode 2) keeps the diffusion limit: the
+    pulse is radiation diffusing through uniform gas, which the magnetofluid block's
+    viscosity does not touch."""
+    sigma, t_end = 100.0, 600.0
+    full = _pulse("pvm", True, sigma, t_end)
+    rad = _pulse("pvm", "radiation", sigma, t_end)
+    print("pulse sigma=100 rel L1: beta on every component %.4e, on the radiation block %.4e" % (full, rad))
+    assert rad < 0.05 and abs(rad - full) <= 0.02 * full
+
+
 def test_pulse_without_damping_is_too_diffusive():
     sigma, t_end = 100.0, 600.0
     good = _pulse("pvm", True, sigma, t_end)

@@ -173,6 +173,21 @@ def test_beta_damps_viscosity():
     np.testing.assert_array_equal(F3, F1)
 
 
+def test_radiation_only_beta_is_beta_on_the_radiation_block():
+    """beta_mode 2 (a variant; the paper leaves other choices of beta open): Eq. beta
+    damps the viscosity of E_r and F_r only.  Its magnetofluid components equal the
+    undamped flux and its radiation components the damped one, bit for bit."""
+    VL = np.array([1.0, 0.1, 0, 0, 1.0, 0.2, 0.1, 0, 1.0, 0.1, 0, 0])
+    VR = np.array([0.5, -0.1, 0.05, 0, 0.3, 0.2, -0.1, 0.1, 0.4, 0.0, 0.1, 0])
+    out = {}
+    for beta in (True, False, "radiation"):
+        P = O.Params(gamma=4 / 3, beta=beta)
+        out[beta] = O.pvm_flux(VL, VR, 5.0, 10.0, 0, P)[0]
+    np.testing.assert_array_equal(out["radiation"][:8], out[False][:8])
+    np.testing.assert_array_equal(out["radiation"][8:], out[True][8:])
+    assert not np.array_equal(out[True][8:], out[False][8:])
+
+
 def _alfven(N, recon):
     P = O.Params(gamma=4 / 3, cfl=0.3, recon=recon)
     A = np.sqrt(2 / (7 + 3 * np.sqrt(5)))
