@@ -135,3 +135,36 @@ def test_fp32_bulk_c1_steps():
     assert not mismatch, mismatch
     assert not bad, bad
     assert len(both_failed) <= 2, both_failed
+
+
+def test_fp32_bulk_c1_full_size_sampled():
+    """The headline workload at full size (4096 instances, 4.49 M cells) in the launch
+    configuration the benchmark times (16 lanes, 64-thread cell blocks): one step, and
+    the smallest, the largest and six random instances against the FP64 oracle one by
+    one, per variable relative L1 <= 1e-5."""
+    from gpu_helpers import oracle_pool_runs
+    w = W.riemann_batch(4096, seed=W.SEED_BASE + 1)
+    ctx = gpu_context(w, precision="fp32_bulk", lanes=16)
+    ctx.set_tuning(cell_block=64, lanes=16)
+    ctx.set_times(np.zeros(w.n_inst), np.full(w.n_inst, np.inf))
+    ctx.imex_step(1)
+    U32 = ctx.get_state()[0].cpu().numpy()
+    st = ctx.inst_status()
+    n = np.array([g["n"][0] for g in w.grids])
+    idx = [int(np.argmin(n)), int(np.argmax(n))] + [
+        int(i) for i in np.random.default_rng(1).choice(w.n_inst, 6, replace=False)]
+    jobs = []
+    for i in idx:
+        g, V, kappa, sigma = w.instance(i)
+        jobs.append((g["n"][0], g["dx"][0], V, kappa, sigma, w.gamma, w.a_rad, w.cfl, np.inf, 1))
+    off = w.cell_offsets()
+    worst = 0.0
+    for i, r in zip(idx, oracle_pool_runs(jobs)):
+        assert (st[i] != 0) == (r[4] != 0), (i, st[i], r[4])
+        if r[4]:
+            continue
+        e = rel_l1(U32[:, off[i]:off[i + 1]], r[0])
+        worst = max(worst, max(e.values()))
+        assert max(e.values()) <= 1e-5, (i, e)
+    print("full-size C1, FP32-bulk, 8 sampled instances: worst per-variable rel L1 %.2e" % worst)
+    assert (st != 0).sum() == 0
