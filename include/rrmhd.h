@@ -33,6 +33,7 @@
 #define RRMHD_H
 
 #include <stdint.h>
+#include <stddef.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -151,6 +152,25 @@ rrmhd_status rrmhd_set_state(rrmhd_ctx* ctx, const double* V);
  * double[12][ncells] each; either may be NULL. */
 rrmhd_status rrmhd_get_state(const rrmhd_ctx* ctx, double* U, double* V);
 
+/* Checkpoints.  A checkpoint holds everything that determines the context's future
+ * steps apart from its grids, options and launch shapes: U and V, kappa and sigma,
+ * the per-cell Jacobian cache of the implicit solve (Sec. 3.3), the staggered face
+ * field (ct = 1), and per instance t, t_end, the last dt, the CFL signal maximum, the
+ * status and the first bad cell.  Restoring it, into the same context or into
+ * another one created with the same grids and options (any launch shapes), and
+ * stepping on gives bit for bit the results of the run that wrote it, which a
+ * restart through rrmhd_set_state (Jacobian cache emptied) does not.
+ * rrmhd_checkpoint_bytes: the size of the buffer (0 for a NULL context).
+ * rrmhd_checkpoint_save: writes into buf, caller-owned device or host memory of that
+ *   size (pinned host memory keeps the copy asynchronous); enqueued on the context's
+ *   stream, so synchronise before reading a host buffer.
+ * rrmhd_checkpoint_restore: reads buf (device or host); synchronises the stream to
+ *   read the header first; RRMHD_EINVAL if the checkpoint was written by a context
+ *   of another layout (instances, cells, faces), precision or ct setting. */
+size_t       rrmhd_checkpoint_bytes(const rrmhd_ctx* ctx);
+rrmhd_status rrmhd_checkpoint_save(rrmhd_ctx* ctx, void* buf);
+rrmhd_status rrmhd_checkpoint_restore(rrmhd_ctx* ctx, const void* buf);
+
 /* Per-instance current time and end time (host, n_inst each); an instance
  * stops once t reaches t_end (the last step is clipped to land on it). */
 rrmhd_status rrmhd_set_times(rrmhd_ctx* ctx, const double* t, const double* t_end);
@@ -171,8 +191,11 @@ rrmhd_status rrmhd_get_inst_status(const rrmhd_ctx* ctx, int32_t* status);
  * admissible state (no con2prim root, or no converged implicit solve) gets the
  * first-order Rusanov flux at its faces and is updated again with its neighbours,
  * in up to three passes (a neighbour that then fails is flagged in turn); only a
- * failure after that freezes the instance.  Enqueued as one CUDA graph per step;
- * returns without synchronising. */
+ * failure after that freezes the instance.  Enqueued as one CUDA graph per step
+ * and lane; the lanes (independent instance ranges) run their nsteps steps back
+ * to back and join the context's stream once, so one call of nsteps steps gives
+ * the same results as nsteps calls of one step, and can take less time.  Returns
+ * without synchronising. */
 rrmhd_status rrmhd_imex_step(rrmhd_ctx* ctx, int nsteps);
 
 /* One step as rrmhd_imex_step takes it, with every instance's dt capped:

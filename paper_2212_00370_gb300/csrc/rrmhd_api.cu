@@ -53,6 +53,7 @@ struct rrmhd_ctx {
   cudaEvent_t fork = nullptr;
   int* d_flag = nullptr;  // one device int (host-buffer entry)
   int* h_flag = nullptr;  // pinned mirror
+  unsigned char ckpt_head[256] = {};  // source of the last checkpoint's header copy
   std::string err;
 };
 
@@ -419,22 +420,30 @@ static rrmhd_status build_step_graph(rrmhd_ctx* c, Lane& L, int cur) {
   return cuda_check(c, e, "cudaGraphInstantiate");
 }
 
-// Each step: the lanes fork from the caller's stream, run their step graph
-// concurrently on their own streams, and join back into it.
+// The lanes fork from the caller's stream, run their nsteps step graphs back to
+// back on their own streams, and join back into it once.  A lane touches only its
+// own instances, cells, faces, edges and counters, so the lanes need no join
+// between steps: a lane held up by a slow implicit solve in one step catches up
+// while the others run ahead, and the results are those of nsteps single steps.
 rrmhd_status rrmhd_imex_step(rrmhd_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return set_err(c, RRMHD_EINVAL, "bad argument");
-  for (int k = 0; k < nsteps; ++k) {
-    RR_CUDA(c, cudaEventRecord(c->fork, c->stream));
-    for (Lane& L : c->lanes) {
-      rrmhd_status s = build_step_graph(c, L, c->cur);
+  if (nsteps == 0) return RRMHD_OK;
+  for (Lane& L : c->lanes)
+    for (int p = 0; p < (nsteps > 1 ? 2 : 1); ++p) {
+      rrmhd_status s = build_step_graph(c, L, c->cur ^ p);
       if (s != RRMHD_OK) return s;
-      RR_CUDA(c, cudaStreamWaitEvent(L.stream, c->fork, 0));
-      RR_CUDA(c, cudaGraphLaunch(L.graph[c->cur], L.stream));
-      RR_CUDA(c, cudaEventRecord(L.done, L.stream));
     }
-    for (Lane& L : c->lanes) RR_CUDA(c, cudaStreamWaitEvent(c->stream, L.done, 0));
-    c->cur ^= 1;
+  RR_CUDA(c, cudaEventRecord(c->fork, c->stream));
+  for (Lane& L : c->lanes) RR_CUDA(c, cudaStreamWaitEvent(L.stream, c->fork, 0));
+  // submitted step by step across the lanes: streams that share a hardware queue
+  // then hold each other up by one step at most
+  for (int k = 0; k < nsteps; ++k)
+    for (Lane& L : c->lanes) RR_CUDA(c, cudaGraphLaunch(L.graph[c->cur ^ (k & 1)], L.stream));
+  for (Lane& L : c->lanes) {
+    RR_CUDA(c, cudaEventRecord(L.done, L.stream));
+    RR_CUDA(c, cudaStreamWaitEvent(c->stream, L.done, 0));
   }
+  c->cur ^= nsteps & 1;
   return RRMHD_OK;
 }
 
@@ -447,6 +456,88 @@ rrmhd_status rrmhd_imex_step_dt(rrmhd_ctx* c, double dt_max, double* dt_taken) {
   RR_CUDA(c, cudaGetLastError());
   if (s != RRMHD_OK) return s;
   return dt_taken ? rrmhd_get_times(c, nullptr, dt_taken) : RRMHD_OK;
+}
+
+// ---------------------------------------------------------------- checkpoints
+// Layout: a 256-byte header, then every part below at a 256-byte-aligned offset.
+namespace {
+
+struct CkptHeader {
+  char magic[8];  // "RRMHDCK1"
+  int32_t precision, ct, n_inst, pad;
+  int64_t ncells, nfaces, bytes;
+};
+
+struct CkptPart {
+  void* dev;
+  size_t bytes;
+};
+
+std::vector<CkptPart> ckpt_parts(const rrmhd_ctx* c) {
+  const size_t N = (size_t)c->L.ncells, n = (size_t)c->L.n_inst;
+  const rr::DeviceBufs& B = c->B;
+  std::vector<CkptPart> p = {{cur_U(c), 96 * N},   {cur_V(c), 96 * N},   {B.kappa, 8 * N},
+                             {B.sigma, 8 * N},     {B.jc, 136 * N},      {B.t, 8 * n},
+                             {B.t_end, 8 * n},     {B.dt, 8 * n},        {B.smax, 8 * n},
+                             {B.status, 4 * n},    {B.bad_cell, 8 * n}};
+  if (c->opts.ct) p.push_back({cur_b(c), 8 * (size_t)c->L.nfaces});
+  return p;
+}
+
+size_t ckpt_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
+CkptHeader ckpt_header(const rrmhd_ctx* c) {
+  CkptHeader h{};
+  std::memcpy(h.magic, "RRMHDCK1", 8);
+  h.precision = c->opts.precision;
+  h.ct = c->opts.ct;
+  h.n_inst = c->L.n_inst;
+  h.ncells = c->L.ncells;
+  h.nfaces = c->L.nfaces;
+  h.bytes = (int64_t)rrmhd_checkpoint_bytes(c);
+  return h;
+}
+
+}  // namespace
+
+size_t rrmhd_checkpoint_bytes(const rrmhd_ctx* c) {
+  if (!c) return 0;
+  size_t s = 256;
+  for (const CkptPart& q : ckpt_parts(c)) s += ckpt_align(q.bytes);
+  return s;
+}
+
+rrmhd_status rrmhd_checkpoint_save(rrmhd_ctx* c, void* buf) {
+  if (!c || !buf) return set_err(c, RRMHD_EINVAL, "bad argument");
+  const CkptHeader h = ckpt_header(c);
+  std::memcpy(c->ckpt_head, &h, sizeof(h));
+  char* dst = static_cast<char*>(buf);
+  RR_CUDA(c, cudaMemcpyAsync(dst, c->ckpt_head, sizeof(h), cudaMemcpyDefault, c->stream));
+  size_t off = 256;
+  for (const CkptPart& q : ckpt_parts(c)) {
+    RR_CUDA(c, cudaMemcpyAsync(dst + off, q.dev, q.bytes, cudaMemcpyDefault, c->stream));
+    off += ckpt_align(q.bytes);
+  }
+  return RRMHD_OK;
+}
+
+rrmhd_status rrmhd_checkpoint_restore(rrmhd_ctx* c, const void* buf) {
+  if (!c || !buf) return set_err(c, RRMHD_EINVAL, "bad argument");
+  CkptHeader h{};
+  const char* src = static_cast<const char*>(buf);
+  RR_CUDA(c, cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDefault, c->stream));
+  RR_CUDA(c, cudaStreamSynchronize(c->stream));
+  const CkptHeader want = ckpt_header(c);
+  if (std::memcmp(h.magic, want.magic, 8) != 0 || h.precision != want.precision ||
+      h.ct != want.ct || h.n_inst != want.n_inst || h.ncells != want.ncells ||
+      h.nfaces != want.nfaces || h.bytes != want.bytes)
+    return set_err(c, RRMHD_EINVAL, "checkpoint: written by a context of another layout or form");
+  size_t off = 256;
+  for (const CkptPart& q : ckpt_parts(c)) {
+    RR_CUDA(c, cudaMemcpyAsync(q.dev, src + off, q.bytes, cudaMemcpyDefault, c->stream));
+    off += ckpt_align(q.bytes);
+  }
+  return RRMHD_OK;
 }
 
 rrmhd_status rrmhd_get_first_bad_cell(const rrmhd_ctx* c, int64_t* cell) {

@@ -100,6 +100,9 @@ _SIGNATURES = [
     ("rrmhd_imex_step_dt", C.c_int, [_VP, C.c_double, _DP]),
     ("rrmhd_get_first_bad_cell", C.c_int, [_VP, C.POINTER(C.c_int64)]),
     ("rrmhd_imex_step_host", C.c_int, [_VP, _VP, _VP, C.c_int]),
+    ("rrmhd_checkpoint_bytes", C.c_size_t, [_VP]),
+    ("rrmhd_checkpoint_save", C.c_int, [_VP, _VP]),
+    ("rrmhd_checkpoint_restore", C.c_int, [_VP, _VP]),
     ("rrmhd_prim2con", C.c_int, [_VP, _VP, _VP, _I64]),
     ("rrmhd_con2prim", C.c_int, [_VP, _VP, _VP, _VP, _VP, _I64]),
     ("rrmhd_flux_sweep", C.c_int, [_VP, C.c_int, _VP]),
@@ -327,6 +330,29 @@ class Context:
         cell = np.zeros(self.n_inst, dtype=np.int64)
         _check(self.ctx, lib().rrmhd_get_first_bad_cell(self.ctx, cell.ctypes.data_as(C.POINTER(C.c_int64))))
         return cell
+
+    def checkpoint_bytes(self):
+        return int(lib().rrmhd_checkpoint_bytes(self.ctx))
+
+    def checkpoint(self, device=True):
+        """A new uint8 tensor (on the device, or pinned on the host) holding a checkpoint
+        of the context; enqueued on the context's stream."""
+        n = self.checkpoint_bytes()
+        buf = (self.torch.empty(n, dtype=self.torch.uint8, device="cuda") if device else
+               self.torch.empty(n, dtype=self.torch.uint8, pin_memory=True))
+        self.checkpoint_save(buf)
+        return buf
+
+    def checkpoint_save(self, buf):
+        """buf: a contiguous uint8 torch tensor of checkpoint_bytes() (device or host)."""
+        assert buf.is_contiguous() and buf.dtype == self.torch.uint8 and buf.numel() >= self.checkpoint_bytes()
+        _check(self.ctx, lib().rrmhd_checkpoint_save(self.ctx, C.c_void_p(buf.data_ptr())))
+
+    def checkpoint_restore(self, buf):
+        """buf: a checkpoint (uint8 tensor); the library checks that its header matches
+        this context's layout, precision and ct setting (RRMHDError EINVAL if not)."""
+        assert buf.is_contiguous() and buf.dtype == self.torch.uint8 and buf.numel() >= 256
+        _check(self.ctx, lib().rrmhd_checkpoint_restore(self.ctx, C.c_void_p(buf.data_ptr())))
 
     def imex_step_host(self, V_in, V_out, nsteps=1):
         """V_in, V_out: host float64 arrays [12][ncells] (pinned torch tensors or numpy)."""

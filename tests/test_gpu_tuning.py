@@ -62,6 +62,30 @@ def test_results_do_not_depend_on_the_launch_shape(precision):
         assert np.array_equal(got[2], ref[2]) and np.array_equal(got[3], ref[3])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_one_call_of_n_steps_equals_n_calls(precision):
+    """Lanes run the steps of one call back to back without joining in between;
+    the result must be that of single steps, also where instances reach t_end at
+    different steps and a lane runs out of live instances."""
+    w = W.riemann_batch(40, seed=23, nmin=20, nmax=300)
+    out = []
+    for calls in ([5], [1] * 5, [2, 3]):
+        ctx = gpu_context(w, precision=precision, lanes=5)
+        ctx.set_times(np.zeros(w.n_inst), np.where(np.arange(w.n_inst) % 3 == 0, 2e-3, np.inf))
+        for n in calls:
+            ctx.imex_step(n)
+        U, V = ctx.get_state()
+        t, dt = ctx.get_times()
+        out.append((U.cpu().numpy(), V.cpu().numpy(), t, dt, ctx.inst_status()))
+        ctx.close()
+    for got in out[1:]:
+        compare_bitwise(got[0], out[0][0], "U")
+        compare_bitwise(got[1], out[0][1], "V")
+        for k in (2, 3, 4):
+            assert np.array_equal(got[k], out[0][k])
+    assert (out[0][2] == 2e-3).sum() > 0          # some instances stopped at t_end
+
+
 def test_shapes_in_2d_and_3d():
     from test_gpu_parity import _periodic_smooth
     for shape_nd in [(24, 20), (10, 8, 6)]:
