@@ -78,27 +78,25 @@ def test_fp32_bulk_c0_to_t_end_within_bounds():
         assert v < trunc[k], (k, v, trunc[k])
 
 
-def test_fp32_bulk_c1_steps():
-    """The headline batch (C1, 4096 instances, seed 2212003701): 256 instances spread
-    evenly over it, 5 steps of the FP32-bulk form against 5 steps of the FP64 oracle.
-    Every instance must meet the bound per variable (relative L1 <= 1e-5); an instance
-    above it must instead be below the oracle's own N-vs-2N difference for that
-    instance (the same problem on 2N cells run to the same time, averaged onto N) in
-    every variable above 1e-5.  Such instances are counted and printed.  An instance
+def _fp32_bulk_vs_oracle(w, steps, lanes=1):
+    """steps of the FP32-bulk form against steps of the FP64 oracle, instance by
+    instance.  Every instance must meet the bound per variable (relative L1 <= 1e-5);
+    an instance above it must instead be below the oracle's own N-vs-2N difference for
+    that instance (the same problem on 2N cells run to the same time, averaged onto N)
+    in every variable above 1e-5.  Such instances are counted and printed.  An instance
     that fails in one form and not in the other fails the test."""
     from gpu_helpers import oracle_pool_runs
-    full = W.riemann_batch(4096, seed=W.SEED_BASE + 1)
-    w = full.subset(list(np.linspace(0, full.n_inst - 1, 256).astype(int)))
-    ctx = gpu_context(w, precision="fp32_bulk")
+    ctx = gpu_context(w, precision="fp32_bulk", lanes=lanes)
     ctx.set_times(np.zeros(w.n_inst), np.full(w.n_inst, np.inf))
-    ctx.imex_step(5)
+    ctx.imex_step(steps)
     U32 = ctx.get_state()[0].cpu().numpy()
     st = ctx.inst_status()
+    ctx.close()
     off = w.cell_offsets()
     jobs = []
     for i in range(w.n_inst):
         g, V, kappa, sigma = w.instance(i)
-        jobs.append((g["n"][0], g["dx"][0], V, kappa, sigma, w.gamma, w.a_rad, w.cfl, np.inf, 5))
+        jobs.append((g["n"][0], g["dx"][0], V, kappa, sigma, w.gamma, w.a_rad, w.cfl, np.inf, steps))
     ref = oracle_pool_runs(jobs)
     mismatch = [i for i in range(w.n_inst) if (ref[i][4] != 0) != (st[i] != 0)]
     both_failed = [i for i in range(w.n_inst) if ref[i][4] != 0 and st[i] != 0]
@@ -128,12 +126,29 @@ def test_fp32_bulk_c1_steps():
             {k: "%.1e" % trunc[k] for k, v in e.items() if v > 1e-5}))
         if over:
             bad.append((i, over))
-    print("C1 256 instances x 5 steps, worst per-variable rel L1:",
+    print("C1 %d instances x %d steps, worst per-variable rel L1:" % (w.n_inst, steps),
           {k: "%.2e" % v for k, v in worst.items()})
     print("instances above 1e-5: %d (all below their N-vs-2N difference: %s); failed in both "
           "forms: %d; failed in one form only: %d" % (len(above), not bad, len(both_failed), len(mismatch)))
     assert not mismatch, mismatch
     assert not bad, bad
+    return above, both_failed
+
+
+def test_fp32_bulk_c1_steps():
+    """The headline batch (C1, 4096 instances, seed 2212003701): 256 instances spread
+    evenly over it, 5 steps of the FP32-bulk form against 5 steps of the FP64 oracle."""
+    full = W.riemann_batch(4096, seed=W.SEED_BASE + 1)
+    w = full.subset(list(np.linspace(0, full.n_inst - 1, 256).astype(int)))
+    _, both_failed = _fp32_bulk_vs_oracle(w, 5)
+    assert len(both_failed) <= 2, both_failed
+
+
+def test_fp32_bulk_c1_whole_batch_12_steps():
+    """All 4096 instances of the headline batch at full size, 12 steps, in the
+    benchmark's lane count: the same bound, instance by instance, against the oracle."""
+    w = W.riemann_batch(4096, seed=W.SEED_BASE + 1)
+    _, both_failed = _fp32_bulk_vs_oracle(w, 12, lanes=16)
     assert len(both_failed) <= 2, both_failed
 
 
