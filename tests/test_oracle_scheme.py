@@ -189,7 +189,13 @@ def test_radiation_only_beta_is_beta_on_the_radiation_block():
 
 
 def _alfven(N, recon):
-    P = O.Params(gamma=4 / 3, cfl=0.3, recon=recon)
+    return _alfven_solver(N, recon, "pvm")
+
+
+def _alfven_solver(N, recon, solver):
+    """L1 error of v_z after one period of the circularly polarized Alfven wave
+    (Sec. 4.1.1), radiation passive, with the given Riemann solver."""
+    P = O.Params(gamma=4 / 3, cfl=0.3, recon=recon, solver=solver)
     A = np.sqrt(2 / (7 + 3 * np.sqrt(5)))
     B0, rho0, p0 = 1.0, 1.0, 1.0
     h0 = 1 + 4 * p0 / rho0
