@@ -42,11 +42,11 @@ sys.path.insert(0, ROOT)
 # of the 4th step (their implicit weights differ, and so does the solve's work), measured
 # with ncu on a 2048-instance sample of the same distribution.
 FP64_INST_PER_ZONE = {"fp64": {"faces": 4832.0, "cells": 4591.0},
-                      "fp32_bulk": {"faces": 4.0, "cells": 2282.0},
+                      "fp32_bulk": {"faces": 4.0, "cells": 2281.0},
                       "fp64_tangent": {"faces": 5238.0, "cells": 4591.0}}
 # DRAM bytes per cell of one launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)
 TRAFFIC_PER_CELL = {"fp64": {"faces": 239.0, "cells": 1669.0},
-                    "fp32_bulk": {"faces": 377.0, "cells": 2311.0},
+                    "fp32_bulk": {"faces": 439.0, "cells": 2293.0},
                     "fp64_tangent": {"faces": 241.0, "cells": 1669.0}}
 # Nominal FP64 rate of GB300: 1.25 TFLOP/s = 6.25e11 FP64-pipe instructions/s
 # (2 per SM per clock on 152 SMs at 2.07 GHz).  The roofline divides by the rate

@@ -3,7 +3,10 @@
 Each translation unit is compiled in parallel with nvcc, then linked as a
 shared library next to this file (in-tree, git-ignored).  The FP64 kernels are
 compiled with --fmad=false: their arithmetic order is part of the
-specification of the FP64 path (bit-reproducible results).
+specification of the FP64 path (bit-reproducible results).  The FP32-bulk unit
+takes FP32 division and square root in their fast forms (-prec-div=false,
+-prec-sqrt=false: ~2 ulp instead of correctly rounded); its FP64 arithmetic is
+unaffected.
 """
 import concurrent.futures as cf
 import os
@@ -24,7 +27,7 @@ UNITS = {
     "rrmhd_f64.cu": ["--fmad=false"],
     "rrmhd_api.cu": [],
     "rrmhd_noalloc.cu": ["--fmad=false"],
-    "rrmhd_f32.cu": [],
+    "rrmhd_f32.cu": ["-prec-div=false", "-prec-sqrt=false"],
     "rrmhd_server.cu": ["--fmad=false"],
     "rrmhd_probe.cu": [],
 }
