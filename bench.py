@@ -15,7 +15,9 @@ batching, time to solution) and the CPU oracle are measured too.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line.  ``value`` is device throughput with the state resident
-in HBM; ``e2e`` the same metric through the C-ABI host-buffer entry
+in HBM, the K timed steps enqueued as one rrmhd_imex_step call; ``p50_ms`` /
+``p99_ms`` are the same K steps again (restored from a checkpoint) one call per
+step; ``e2e`` the same K steps once more through the C-ABI host-buffer entry
 (rrmhd_imex_step_host: H2D of the state, the step, D2H of the primitives, every
 step).  N > 1 (torchrun): every rank advances its own batch (seed + rank):
 independent problems, no data-path collective, weak scaling.
