@@ -50,7 +50,7 @@ def _stale():
 
 def _compile(unit, flags, verbose):
     obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
-    extra = os.environ.get("RRMHD_NVCC_FLAGS", "").split()   # tuning knobs, e.g. -DRR_CELL_MIN_BLOCKS=2
+    extra = os.environ.get("RRMHD_NVCC_FLAGS", "").split()   # tuning knobs, e.g. -DRR_F64_CELL_WARPS=12
     cmd = [NVCC, *ARCH, *COMMON, *flags, *extra, "-c", os.path.join(CSRC, unit), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

@@ -28,14 +28,18 @@ using namespace idx;
 
 constexpr int kFaceThreads = 128;
 constexpr int kCellThreads = 128;
-// Resident blocks per SM requested from the register allocator (launch-bounds
-// tuning knobs; 255 registers per thread at 1).
-#ifndef RR_FACE_MIN_BLOCKS
-#define RR_FACE_MIN_BLOCKS 1
+// Resident warps per SM requested from the register allocator for the face and cell
+// kernels (launch-bounds tuning knobs): 0 leaves the registers unbounded (255 per
+// thread, 8 warps per SM); W > 0 asks for W warps per SM in blocks of BS threads (at
+// most 32 resident blocks per SM).
+#ifndef RR_F64_FACE_WARPS
+#define RR_F64_FACE_WARPS 0
 #endif
-#ifndef RR_CELL_MIN_BLOCKS
-#define RR_CELL_MIN_BLOCKS 1
+#ifndef RR_F64_CELL_WARPS
+#define RR_F64_CELL_WARPS 0
 #endif
+#define RR_F64_BLOCKS(W, BS) \
+  ((W) == 0 ? 1 : ((((W) * 32 + (BS) - 1) / (BS)) > 32 ? 32 : (((W) * 32 + (BS) - 1) / (BS))))
 
 // PVM flux with exact tangent products A w (the FP64 tangent variant): the same
 // reconstruction, central fluxes, con2prim of U_m and beta as pvm_flux, only the
@@ -237,22 +241,22 @@ static __device__ __noinline__ void cell_item(const StageArgs& a, int64_t c) {
 }
 
 template <int BS, int PT>
-__global__ void __launch_bounds__(BS, RR_FACE_MIN_BLOCKS) k_faces(StageArgs a) {
+__global__ void __launch_bounds__(BS, RR_F64_BLOCKS(RR_F64_FACE_WARPS, BS)) k_faces(StageArgs a) {
   grid_items<BS, PT>(lane_faces(a.b), [&](int64_t t) { face_item(a, t); });
 }
 
 template <int BS>
-__global__ void __launch_bounds__(BS, 1) k_faces_persistent(StageArgs a) {
+__global__ void __launch_bounds__(BS, RR_F64_BLOCKS(RR_F64_FACE_WARPS, BS)) k_faces_persistent(StageArgs a) {
   persistent_items(lane_faces(a.b), a.work, [&](int64_t t) { face_item(a, t); });
 }
 
 template <int BS, int PT>
-__global__ void __launch_bounds__(BS, RR_CELL_MIN_BLOCKS) k_cells(StageArgs a) {
+__global__ void __launch_bounds__(BS, RR_F64_BLOCKS(RR_F64_CELL_WARPS, BS)) k_cells(StageArgs a) {
   grid_items<BS, PT>(a.b.c_end - a.b.c_begin, [&](int64_t t) { cell_item(a, a.b.c_begin + t); });
 }
 
 template <int BS>
-__global__ void __launch_bounds__(BS, 1) k_cells_persistent(StageArgs a) {
+__global__ void __launch_bounds__(BS, RR_F64_BLOCKS(RR_F64_CELL_WARPS, BS)) k_cells_persistent(StageArgs a) {
   persistent_items(a.b.c_end - a.b.c_begin, a.work + 1,
                    [&](int64_t t) { cell_item(a, a.b.c_begin + t); });
 }
@@ -364,7 +368,7 @@ __device__ __forceinline__ void fallback_cell(const StageArgs& a, int64_t c, int
   }
 }
 
-__global__ void __launch_bounds__(kCellThreads, RR_CELL_MIN_BLOCKS) k_fallback_cells(StageArgs a) {
+__global__ void __launch_bounds__(kCellThreads, RR_F64_BLOCKS(RR_F64_CELL_WARPS, kCellThreads)) k_fallback_cells(StageArgs a) {
   const int64_t c = a.b.c_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int inst = -1;
   double s = 0.0;
